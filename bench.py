@@ -1,0 +1,393 @@
+"""Benchmark of the SRP hot path on GB300.
+
+One step = one srp_map call (PHAT cross spectra -> critical GCC samples ->
+sinc-interpolation contraction with the pair sum -> argmax) over one batch
+of L = 64 STFT frames of the 3D room workload: M = 8 microphones uniform in a
+0.5 m cube at the centre of a 5 x 4 x 3 m room, a 100 x 80 x 60 grid of cell
+centres at 0.05 m (J = 480000 candidates, Q = 28 pairs), fs = 16 kHz,
+K = 1024, N_aux = 2, FP32.  Inputs are synthetic free-field white-noise
+scenes (SNR 10 dB), resident in HBM before the timed region; L2 is flushed
+(256 MB write) between timed steps.
+
+Metric: SRP cells*pairs/s = J * Q * L / step time (whole job: summed over
+ranks, max time over ranks).  The conventional SRP path is timed beside it
+on the same inputs; e2e times srp_map_host with pinned host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SRP cells*pairs/s (Nyquist vs conventional) at stated map error; p50/p99 ms"
+UNIT = "cells*pairs/s"
+WORKLOAD = dict(name="room_3d", M=8, J=480000, K=1024, L=64, n_aux=2, fs=16000.0, snr_db=10.0)
+FLUSH_BYTES = 256 << 20
+
+
+def config_dict(Q, S):
+    w = WORKLOAD
+    return {
+        "workload": (f"room_3d: M={w['M']} mics uniform in a 0.5 m cube centred in a 5x4x3 m "
+                     f"room, 100x80x60 grid at 0.05 m (J={w['J']}), Q={Q} pairs, fs=16 kHz, "
+                     f"K={w['K']}, L={w['L']} frames per step, N_aux={w['n_aux']} (S={S} "
+                     f"critical samples), FP32, free-field white noise at SNR 10 dB"),
+        "candidates": w["J"], "pairs": Q, "frames_per_step": w["L"], "K": w["K"],
+        "n_aux": w["n_aux"], "S": S, "precision": "fp32",
+        "l2": "flushed between timed steps (256 MB write)",
+    }
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; independent batches per rank)
+# --------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a float over ranks (identity when world == 1)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    QUERY = ("clocks.sm,clocks.max.sm,utilization.gpu,power.draw,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.lines, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) != 8:
+                continue
+            try:
+                rows.append((float(p[0]), float(p[1]), float(p[2]), p[4:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        loaded = [r for r in rows if r[2] >= 30.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in loaded for k, v in enumerate(r[3])
+                          if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in loaded])),
+                "sm_max_mhz": float(max(r[1] for r in loaded)),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+
+def make_batches(rank: int, n: int):
+    from paper_2012_09499_gb300 import synth
+    cfgs = [synth.room_3d(seed=1000 * rank + s) for s in range(n)]
+    # one geometry (the plan) per rank; every batch shares it
+    mic, grid = cfgs[0]["mic"], cfgs[0]["grid"]
+    rng = np.random.default_rng(77 + rank)
+    Ys = [cfgs[0]["Y"]]
+    for s in range(1, n):
+        src = rng.uniform([0.3, 0.3, 0.3], [4.7, 3.7, 2.7])
+        Ys.append(synth.free_field_stft(rng, mic, [src], 16000.0, 1024, 64, 10.0))
+    return mic, grid, Ys
+
+
+def time_steps(step, steps, warmup, flush, stream, world, timed_stage=None):
+    """Runs warmup + steps; returns per-step device ms (CUDA events on the
+    launching stream, L2 flushed before each step) and, if timed_stage is
+    given, per-step ms of that stage from the library's own events."""
+    import torch
+    for w in range(warmup):
+        step(w)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stage_ms = []
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        flush(k)
+        ev0[k].record(stream)
+        step(k)
+        ev1[k].record(stream)
+        if timed_stage is not None:
+            stage_ms.append(timed_stage())
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    return ms, np.array(stage_ms), wall
+
+
+def bench_ours(args):
+    import torch
+
+    from paper_2012_09499_gb300 import srp
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    w = WORKLOAD
+    mic, grid, Ys = make_batches(rank, 4)
+    L, J = w["L"], w["J"]
+    d_in = [torch.from_numpy(Y).to(dev) for Y in Ys]
+    maps = torch.empty((L, J), dtype=torch.float32, device=dev)
+    am = torch.empty(L, dtype=torch.int32, device=dev)
+    pk = torch.empty(L, dtype=torch.float32, device=dev)
+    flush_buf = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush(k):
+        flush_buf.fill_(float(k))
+
+    plans = {}
+    for mode in ("nyquist", "conventional"):
+        plans[mode] = srp.Plan(mic, grid, w["fs"], 343.0, w["K"], mode=mode, n_aux=w["n_aux"],
+                               max_frames=L, host_io=(mode == "nyquist"))
+        srp.srp_set_timing(plans[mode].handle, True)
+    ny = plans["nyquist"]
+    Q, S = ny.info.Q, ny.info.S
+
+    def make_step(plan):
+        def step(k):
+            srp.srp_map(plan.handle, d_in[k % len(d_in)], L, maps, am, pk, stream)
+        return step
+
+    def stage_time(plan):
+        return lambda: srp.srp_stage_times(plan.handle)["map"]
+
+    res = {}
+    with ClockSampler(local) as clk:
+        for mode, plan in plans.items():
+            steps = args.steps if mode == "nyquist" else max(3, min(args.steps, args.conv_steps))
+            ms, st, wall = time_steps(make_step(plan), steps, args.warmup, flush, stream, world,
+                                      stage_time(plan))
+            launches = srp.srp_last_launch_count(plan.handle) * steps
+            res[mode] = dict(ms=ms, stage=st, wall=wall, steps=steps, launches=launches)
+    clocks = clk.summary()
+
+    # map error of the Nyquist approximation w.r.t. conventional on one batch
+    mc = torch.empty_like(maps)
+    srp.srp_map(plans["conventional"].handle, d_in[0], L, mc, am, pk, stream)
+    srp.srp_map(ny.handle, d_in[0], L, maps, am, pk, stream)
+    torch.cuda.synchronize()
+    num = ((mc.double() - maps.double()) ** 2).sum(dim=1)
+    den = (mc.double() ** 2).sum(dim=1)
+    e_appr = (10.0 * torch.log10(num / den)).cpu().numpy()
+
+    # end to end through the host entry point (pinned buffers, copies timed)
+    h_in = [torch.from_numpy(Y).pin_memory() for Y in Ys]
+    h_maps = torch.empty((L, J), dtype=torch.float32).pin_memory()
+    h_am = torch.empty(L, dtype=torch.int32).pin_memory()
+    h_pk = torch.empty(L, dtype=torch.float32).pin_memory()
+    srp.srp_set_timing(ny.handle, False)
+    e2e_steps = max(3, min(args.steps, 20))
+    for k in range(args.warmup):
+        srp.srp_map_host(ny.handle, h_in[k % 4], L, h_maps, h_am, h_pk, stream)
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        srp.srp_map_host(ny.handle, h_in[k % 4], L, h_maps, h_am, h_pk, stream)
+    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, world, dev if world > 1 else None)
+
+    cells = J * Q * L
+    ny_ms = reduce_max(res["nyquist"]["ms"].mean(), world, dev if world > 1 else None)
+    cv_ms = reduce_max(res["conventional"]["ms"].mean(), world, dev if world > 1 else None)
+    k3_ms = float(np.mean(res["nyquist"]["stage"]))
+    flops = 2.0 * J * S * L  # multiply-adds of the interpolation contraction, C_int x L
+    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12  # CUDA-core FP32 FMA rate at the max SM clock
+    achieved = flops / (k3_ms * 1e-3) / 1e12
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu else cpu_baseline(mic, grid, Ys[0], w, Q, S)
+    line = {
+        "metric": METRIC, "value": world * cells / (ny_ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ny_ms,
+        "p50_ms": float(np.percentile(res["nyquist"]["ms"], 50)),
+        "p99_ms": float(np.percentile(res["nyquist"]["ms"], 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic free-field white-noise scenes (seeded), random array geometry",
+        "config": config_dict(Q, S),
+        "conventional": {
+            "value": world * cells / (cv_ms * 1e-3), "ms_per_step": cv_ms,
+            "steps": res["conventional"]["steps"],
+            "p50_ms": float(np.percentile(res["conventional"]["ms"], 50)),
+            "p99_ms": float(np.percentile(res["conventional"]["ms"], 99)),
+            "map_ms": float(np.mean(res["conventional"]["stage"])),
+        },
+        "speedup_nyquist_over_conventional": cv_ms / ny_ms,
+        "e_appr_db": {"median": float(np.median(e_appr)), "max": float(np.max(e_appr))},
+        "map_error_bound": "FP32 path: max |map - FP64 oracle| <= 1e-4 x peak (tests)",
+        "stage_ms": {k: v for k, v in srp.srp_stage_times(plans["conventional"].handle).items()},
+        "roofline": {
+            "kernel": "k_interp_simt (sinc interpolation + pair sum, FP32 CUDA cores)",
+            "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "algorithmic": f"2*J*S*L = {flops:.4g} flop per launch; {k3_ms:.4f} ms per launch",
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts x max clock)",
+        },
+        "e2e": {"value": world * cells / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                "h2d_bytes_per_step": int(L * w["M"] * (w["K"] // 2 + 1) * 8),
+                "d2h_bytes_per_step": int(L * J * 4 + L * 8),
+                "api": "srp_map_host (pinned host buffers; maps, argmax, peak copied back)"},
+        "gpu_launches": int(res["nyquist"]["launches"]),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+# FP64 oracle on the host cores (CPU baseline and reference arm)
+# --------------------------------------------------------------------------
+
+def oracle_step_seconds(mic, grid, Y, w, stride, frames=1):
+    """Times the oracle's Nyquist path on `frames` frames and every
+    `stride`-th candidate; returns (seconds extrapolated to one full step of
+    L frames and J candidates, sample description, threads)."""
+    from oracle import oracle
+    sub = grid[::stride]
+    t0 = time.perf_counter()
+    x = oracle.tdoa(mic, sub, w["fs"], 343.0)
+    t_tdoa = time.perf_counter() - t0  # plan-time work, not counted per step
+    Nq, _ = oracle.lag_counts(mic, w["fs"], 343.0)
+    t0 = time.perf_counter()
+    psi = oracle.phat(Y[:frames])
+    xi = oracle.gcc_samples(psi, Nq, w["n_aux"], w["K"])
+    t_frame = (time.perf_counter() - t0) / frames
+    t0 = time.perf_counter()
+    oracle.nyquist(xi, Nq, w["n_aux"], x)
+    t_interp = (time.perf_counter() - t0) / frames
+    per_frame = t_frame + t_interp * (grid.shape[0] / sub.shape[0])
+    desc = (f"Nyquist path on {frames} frame(s) x {sub.shape[0]} candidates (every "
+            f"{stride}th), extrapolated to J={grid.shape[0]} by the exact J*S interpolation "
+            f"count and to L={w['L']} frames; TDOA table ({t_tdoa:.2f} s) is plan-time")
+    return per_frame * w["L"], desc, oracle.get_threads()
+
+
+def cpu_baseline(mic, grid, Y, w, Q, S):
+    secs, desc, threads = oracle_step_seconds(mic, grid, Y, w, stride=8, frames=2)
+    return {"value": w["J"] * Q * w["L"] / secs, "unit": UNIT, "cores": threads,
+            "kind": "oracle", "sample": desc}
+
+
+def bench_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle
+    w = WORKLOAD
+    mic, grid, Ys = make_batches(0, 1)
+    Q = w["M"] * (w["M"] - 1) // 2
+    Nq, _ = oracle.lag_counts(mic, w["fs"], 343.0)
+    S = int(np.sum(2 * Nq + 2 * w["n_aux"] + 1))
+    for _ in range(args.warmup):
+        oracle_step_seconds(mic, grid, Ys[0], w, stride=64, frames=1)
+    secs = []
+    desc, threads = "", 0
+    for _ in range(args.steps):
+        s, desc, threads = oracle_step_seconds(mic, grid, Ys[0], w, stride=64, frames=1)
+        secs.append(s)
+    ms = 1e3 * float(np.mean(secs))
+    value = w["J"] * Q * w["L"] / (ms * 1e-3)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic free-field white-noise scenes (seeded)", "config": config_dict(Q, S),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--conv-steps", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

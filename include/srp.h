@@ -1,0 +1,196 @@
+/*
+ * srp.h -- C ABI of the GB300 steered response power (SRP) mapping library.
+ *
+ * Computes, per STFT frame, the SRP map of J candidate locations from the
+ * PHAT-weighted cross spectra of all Q = M(M-1)/2 microphone pairs, either
+ * conventionally (Sec. 2.3-2.4: the GCC of every pair evaluated at every
+ * candidate's TDOA by a discrete inverse Fourier transform, Eq. GCC_IFT and
+ * Eq. SRP_T_IFT) or by the Nyquist-Shannon approximation (Sec. 3: each GCC
+ * sampled at the critical lags covering its bounded TDOA interval, then
+ * interpolated with a truncated sinc series, Eq. SRPapprox, and summed over
+ * pairs), followed by the per-frame maximiser (Sec. 2.2).
+ *
+ * Units and conventions (they fix the constant factors the paper leaves open):
+ *  - K is the DFT length (even); inputs carry Kb = K/2 + 1 one-sided bins.
+ *  - The critical sampling period is T = 1/fs (omega_0 = pi fs, Sec. 3.1);
+ *    TDOAs and lags are measured in samples.
+ *  - Pairs q <-> (m, m'), m > m', enumerated m' = 0..M-2 (outer),
+ *    m = m'+1..M-1 (inner); psi_q(k) = y_m(k) y_m'(k)^* / |y_m(k) y_m'(k)^*|
+ *    (Eq. corrmatrix with the PHAT weight), 0 where the denominator is 0.
+ *  - The map value is sum_q xi_q(x_iq) with
+ *    xi_q(x) = (1/K) sum_{k=0}^{K/2} a_k Re[psi_q(k) e^{j 2 pi k x / K}],
+ *    a_0 = a_{K/2} = 1 and a_k = 2 otherwise (the two-sided frequency
+ *    integral of Eq. SRP_T without its constant factor 2).
+ *  - Nyquist mode samples xi_q at n = -(N_q+N_aux) .. N_q+N_aux with
+ *    N_q = floor(d_q fs / c) (Eq. SRPapprox) and interpolates with
+ *    sinc(u) = sin(pi u)/(pi u).
+ *
+ * Memory: the library copies the geometry, builds every plan table on the
+ * device and owns it together with the scratch buffers a call needs; the
+ * caller owns all input and output buffers.  Device pointers are plain CUDA
+ * device addresses on the device that was current when the plan was built.
+ *
+ * Execution: srp_map and the other stage entry points only enqueue work on
+ * the given stream and return; they never synchronise.  Calls on one handle
+ * share its scratch buffers and must be ordered (one stream, or the caller
+ * synchronises between streams).  Distinct handles are independent.
+ *
+ * Errors are returned as srp_status codes, never thrown or trapped; a
+ * failing CUDA call maps to SRP_ERR_CUDA and srp_last_error_message() holds
+ * the CUDA error text for the calling thread.
+ */
+#ifndef SRP_H
+#define SRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SRP_API __attribute__((visibility("default")))
+#else
+#define SRP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *srp_stream_t;
+
+typedef enum {
+    SRP_OK = 0,
+    SRP_ERR_INVALID_ARG = 1, /* an argument is out of range or NULL */
+    SRP_ERR_OOM = 2,         /* a device or host allocation failed */
+    SRP_ERR_CUDA = 3,        /* a CUDA call failed (see srp_last_error_message) */
+    SRP_ERR_UNSUPPORTED = 4, /* valid request this build does not implement */
+    SRP_ERR_TIMEOUT = 5      /* a bounded device wait gave up */
+} srp_status;
+
+typedef enum {
+    SRP_MODE_CONV = 1,   /* conventional SRP, Sec. 2.3-2.4 */
+    SRP_MODE_NYQUIST = 2 /* Nyquist-Shannon approximation, Sec. 3.2 */
+} srp_mode;
+
+typedef enum {
+    SRP_PREC_FP32 = 0, /* contractions in FP32 arithmetic */
+    SRP_PREC_BF16 = 1, /* contraction operands in BF16, FP32 accumulation */
+    SRP_PREC_FP16 = 2  /* contraction operands in FP16, FP32 accumulation */
+} srp_precision;
+
+typedef enum {
+    SRP_GRID_POINTS = 0,    /* candidates are points q_i (near field, Eq. Deltat_i) */
+    SRP_GRID_DIRECTIONS = 1 /* candidates are unit vectors r_i (far field, Eq. Deltat_i_spher) */
+} srp_grid_kind;
+
+typedef enum {
+    SRP_IN_STFT = 0, /* input y[L][M][Kb] complex64 (interleaved re, im) STFT frames */
+    SRP_IN_CROSS = 1 /* input psi[L][Q][Kb] complex64 cross spectra, already weighted */
+} srp_input_kind;
+
+typedef struct {
+    int32_t M;                /* microphones, 2 <= M <= 64 */
+    const double *mic_xyz;    /* host [M][3] metres; copied by srp_plan */
+    srp_grid_kind grid_kind;  /* points or far-field directions */
+    int64_t J;                /* candidates, 1 <= J <= 2^31 - 2^20 */
+    const double *grid_xyz;   /* host [J][3] metres or unit vectors; copied */
+    double fs;                /* sampling rate in Hz (> 0); T = 1/fs */
+    double c;                 /* speed of sound in m/s (> 0) */
+    int32_t K;                /* DFT length, even, 4 <= K <= 8192 */
+    srp_mode mode;            /* conventional or Nyquist */
+    int32_t n_aux;            /* auxiliary samples N_aux >= 0 (Nyquist only) */
+    srp_precision precision;  /* arithmetic of the map contraction */
+    srp_input_kind input_kind;/* STFT frames or ready cross spectra */
+    int32_t max_frames;       /* largest L a call may pass, >= 1 */
+    int32_t host_io;          /* nonzero: also size staging buffers for srp_map_host */
+} srp_plan_desc;
+
+/* Sizes of a plan, computed on the host (no device needed). */
+typedef struct {
+    int32_t M, Q, K, Kb;
+    int64_t J;
+    int32_t n_aux;
+    int32_t S;           /* total critical samples sum_q (2 N_q + 2 N_aux + 1); 0 for conventional */
+    int32_t max_nq;      /* max_q N_q */
+    int32_t x_frac_bits; /* fractional bits of the fixed-point TDOA table */
+    int32_t max_frames;
+    size_t device_bytes; /* bytes srp_plan allocates on the device */
+} srp_plan_info;
+
+typedef struct srp_plan_s *srp_handle;
+
+/* Validate a descriptor and report its sizes and the lag count N_q of every
+ * pair (Nq_out: host [Q] or NULL).  N_q = floor(d_q fs / c) follows
+ * Eq. SRPapprox with T = 1/fs.  Host only: touches no device.            */
+SRP_API srp_status srp_plan_describe(const srp_plan_desc *d, srp_plan_info *info, int32_t *Nq_out);
+
+/* Device bytes srp_plan would allocate for d (host only).                */
+SRP_API srp_status srp_plan_footprint(const srp_plan_desc *d, size_t *device_bytes);
+
+/* Build a plan on the current device: pair table, TDOAs of every candidate
+ * and pair (Eq. Deltat_i or Eq. Deltat_i_spher, computed in FP64 and stored
+ * as fixed point of x = Delta t / T), lag tables (Eq. SRPapprox), twiddles
+ * and scratch.  *out is set only on SRP_OK.  The only blocking call.     */
+SRP_API srp_status srp_plan(const srp_plan_desc *d, srp_handle *out);
+
+/* Sizes of a built plan.                                                  */
+SRP_API srp_status srp_plan_get_info(srp_handle h, srp_plan_info *info);
+
+/* Copy the plan's TDOA table back, decoded to samples: host x[J][Q]
+ * (double).  Synchronous; for checking the plan against its definition.  */
+SRP_API srp_status srp_plan_tdoa(srp_handle h, double *x_host);
+
+/* The whole hot path for L frames (0 <= L <= max_frames), Sec. 3.2 order:
+ *   d_in    device input, layout per input_kind (read only);
+ *   d_maps  device [L][J] float maps, row-major by frame, or NULL to skip
+ *           writing maps (argmax and peak are still produced);
+ *   d_argmax device [L] int32: lowest-index maximiser of each frame's map;
+ *   d_peak  device [L] float map value at d_argmax, or NULL.
+ * Asynchronous on stream s.                                               */
+SRP_API srp_status srp_map(srp_handle h, const void *d_in, int32_t L, float *d_maps,
+                   int32_t *d_argmax, float *d_peak, srp_stream_t s);
+
+/* srp_map from and to host memory (pinned memory makes the copies
+ * asynchronous): copies h_in to the plan's staging buffer, runs srp_map,
+ * copies results back and synchronises s before returning.  Needs a plan
+ * built with host_io != 0.  h_maps and h_peak may be NULL.                */
+SRP_API srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps,
+                        int32_t *h_argmax, float *h_peak, srp_stream_t s);
+
+/* First stage alone: PHAT cross spectra psi[L][Q][Kb] complex64 from STFT
+ * frames y[L][M][Kb] (Eq. corrmatrix with the PHAT weight of Sec. 2.1).
+ * Plan must take SRP_IN_STFT.  Asynchronous on s.                         */
+SRP_API srp_status srp_cross_spectra(srp_handle h, const void *d_y, int32_t L, void *d_psi,
+                             srp_stream_t s);
+
+/* Critical GCC samples of a Nyquist plan (Sec. 3.2, first step): for each
+ * frame and pair q, xi_q(n) for n = -(N_q+N_aux)..N_q+N_aux, pairs
+ * concatenated in pair order, written as float d_xi[L][S].  Input as for
+ * srp_map.  Asynchronous on s.                                            */
+SRP_API srp_status srp_gcc_samples(srp_handle h, const void *d_in, int32_t L, float *d_xi,
+                           srp_stream_t s);
+
+/* Per-stage timing: when enabled, srp_map records CUDA events around each
+ * stage on its stream; srp_stage_times waits for the last call's events and
+ * returns milliseconds per stage in ms[0..n): 0 cross spectra, 1 GCC
+ * samples, 2 map contraction, 3 argmax reduction (0 for a skipped stage). */
+SRP_API srp_status srp_set_timing(srp_handle h, int32_t enable);
+SRP_API srp_status srp_stage_times(srp_handle h, float *ms, int32_t n);
+
+/* Number of kernels the last srp_map call launched.                       */
+SRP_API srp_status srp_last_launch_count(srp_handle h, int32_t *n);
+
+/* Release every device and host resource of the plan.  NULL is a no-op.  */
+SRP_API srp_status srp_destroy(srp_handle h);
+
+/* Static description of a status code.                                    */
+SRP_API const char *srp_status_string(srp_status s);
+
+/* Detail of the calling thread's most recent error ("" if none).          */
+SRP_API const char *srp_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRP_H */

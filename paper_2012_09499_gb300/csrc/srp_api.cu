@@ -1,0 +1,559 @@
+// Host side of the SRP library: descriptor validation, the FP64 planner
+// (pairs, lag counts, TDOA tables, twiddles), device memory ownership and
+// the C-ABI entry points that enqueue the kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "srp_internal.h"
+
+namespace srp {
+namespace {
+
+thread_local std::string g_err;
+
+constexpr int kMaxM = 64;
+constexpr int kMaxK = 8192;
+constexpr int kMaxFrames = 65536;
+constexpr int64_t kMaxJ = (int64_t)INT32_MAX - (1 << 20);
+constexpr int kMaxLagSpan = 8192;  // 2 (N_q + N_aux) + 1 per pair
+
+srp_status fail(srp_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+srp_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SRP_ERR_OOM : SRP_ERR_CUDA;
+}
+
+#define SRP_CUDA(call, what)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, (what));   \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+bool finite3(const double *p) { return isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]); }
+
+// Validate the descriptor and compute every size of the plan.  Host only.
+srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
+    if (d == nullptr) return fail(SRP_ERR_INVALID_ARG, "descriptor is NULL");
+    if (d->M < 2 || d->M > kMaxM) return fail(SRP_ERR_INVALID_ARG, "M must be in [2, 64]");
+    if (d->mic_xyz == nullptr) return fail(SRP_ERR_INVALID_ARG, "mic_xyz is NULL");
+    if (d->J < 1 || d->J > kMaxJ) return fail(SRP_ERR_INVALID_ARG, "J out of range");
+    if (d->grid_xyz == nullptr) return fail(SRP_ERR_INVALID_ARG, "grid_xyz is NULL");
+    if (!(d->fs > 0.0) || !isfinite(d->fs)) return fail(SRP_ERR_INVALID_ARG, "fs must be > 0");
+    if (!(d->c > 0.0) || !isfinite(d->c)) return fail(SRP_ERR_INVALID_ARG, "c must be > 0");
+    if (d->K < 4 || d->K > kMaxK || (d->K & 1))
+        return fail(SRP_ERR_INVALID_ARG, "K must be even and in [4, 8192]");
+    if (d->mode != SRP_MODE_CONV && d->mode != SRP_MODE_NYQUIST)
+        return fail(SRP_ERR_INVALID_ARG, "unknown mode");
+    if (d->n_aux < 0) return fail(SRP_ERR_INVALID_ARG, "n_aux must be >= 0");
+    if (d->precision != SRP_PREC_FP32 && d->precision != SRP_PREC_BF16 &&
+        d->precision != SRP_PREC_FP16)
+        return fail(SRP_ERR_INVALID_ARG, "unknown precision");
+    if (d->input_kind != SRP_IN_STFT && d->input_kind != SRP_IN_CROSS)
+        return fail(SRP_ERR_INVALID_ARG, "unknown input kind");
+    if (d->grid_kind != SRP_GRID_POINTS && d->grid_kind != SRP_GRID_DIRECTIONS)
+        return fail(SRP_ERR_INVALID_ARG, "unknown grid kind");
+    if (d->max_frames < 1 || d->max_frames > kMaxFrames)
+        return fail(SRP_ERR_INVALID_ARG, "max_frames must be in [1, 65536]");
+    for (int m = 0; m < d->M; ++m)
+        if (!finite3(d->mic_xyz + 3 * m)) return fail(SRP_ERR_INVALID_ARG, "mic_xyz not finite");
+
+    lay = Layout();
+    lay.M = d->M;
+    lay.Q = d->M * (d->M - 1) / 2;
+    lay.K = d->K;
+    lay.Kb = d->K / 2 + 1;
+    lay.n_aux = d->mode == SRP_MODE_NYQUIST ? d->n_aux : 0;
+    lay.J = d->J;
+    lay.J_pad = round_up(d->J, kTileJ);
+    lay.n_tiles = (int)(lay.J_pad / kTileJ);
+    lay.L_max = d->max_frames;
+    lay.L_pad = (int)round_up(d->max_frames, kFramePad);
+
+    // Pairs (m > m', m' outer) and lag counts N_q = floor(d_q fs / c).
+    double max_bound = 0.0;
+    for (int mp = 0; mp < d->M - 1; ++mp)
+        for (int m = mp + 1; m < d->M; ++m) {
+            const double *a = d->mic_xyz + 3 * m, *b = d->mic_xyz + 3 * mp;
+            const double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+            const double dq = sqrt(dx * dx + dy * dy + dz * dz);
+            const double bound = dq / d->c * d->fs;
+            if (bound > 1.0e6) return fail(SRP_ERR_UNSUPPORTED, "array aperture too large for fs/c");
+            lay.pm.push_back(m);
+            lay.pmp.push_back(mp);
+            lay.Nq.push_back((int32_t)floor(bound));
+            max_bound = std::max(max_bound, bound);
+        }
+    lay.max_nq = *std::max_element(lay.Nq.begin(), lay.Nq.end());
+    int64_t S = 0;
+    if (d->mode == SRP_MODE_NYQUIST) {
+        for (int q = 0; q < lay.Q; ++q) {
+            const int64_t span = 2 * (int64_t)lay.Nq[q] + 2 * (int64_t)d->n_aux + 1;
+            if (span > kMaxLagSpan)
+                return fail(SRP_ERR_UNSUPPORTED, "2(N_q + N_aux) + 1 exceeds 8192 lags");
+            lay.off.push_back((int32_t)S);
+            S += span;
+        }
+    } else {
+        lay.off.assign(lay.Q, 0);
+    }
+    lay.S = (int)S;
+    lay.S_pad = (int)round_up(S, kLagPad);
+
+    // Fixed-point TDOA: the largest xf <= 24 with (max|x| + 2) 2^xf < 2^31.
+    // Far-field directions must be unit vectors so that |x| <= d fs / c.
+    int xf = 24;
+    while (xf > 8 && (max_bound + 2.0) * ldexp(1.0, xf) >= 2147483648.0) --xf;
+    if ((max_bound + 2.0) * ldexp(1.0, xf) >= 2147483648.0)
+        return fail(SRP_ERR_UNSUPPORTED, "TDOA range too large");
+    lay.xf = xf;
+
+    const bool nyq = d->mode == SRP_MODE_NYQUIST;
+    const bool half = d->precision != SRP_PREC_FP32;
+    lay.b_pairs = sizeof(int2) * lay.Q;
+    lay.b_nq = sizeof(int32_t) * lay.Q;
+    lay.b_off = sizeof(int32_t) * lay.Q;
+    lay.b_x = sizeof(int32_t) * (size_t)lay.Q * (size_t)lay.J_pad;
+    lay.b_twid = nyq ? sizeof(float2) * lay.K : 0;
+    lay.b_psi = d->input_kind == SRP_IN_STFT
+                    ? sizeof(float2) * (size_t)lay.L_max * lay.Q * lay.Kb : 0;
+    lay.b_xi = nyq ? sizeof(float) * (size_t)lay.S_pad * lay.L_pad : 0;
+    lay.b_xi16 = (nyq && half) ? sizeof(uint16_t) * (size_t)lay.S_pad * lay.L_pad : 0;
+    lay.b_part = sizeof(unsigned long long) * (size_t)lay.L_pad * lay.n_tiles;
+    if (d->host_io) {
+        const int rows = d->input_kind == SRP_IN_STFT ? lay.M : lay.Q;
+        lay.b_in_stage = sizeof(float2) * (size_t)lay.L_max * rows * lay.Kb;
+        lay.b_maps_stage = sizeof(float) * (size_t)lay.L_max * (size_t)lay.J;
+        lay.b_small_stage = 2 * sizeof(float) * (size_t)lay.L_pad;
+    }
+    return SRP_OK;
+}
+
+srp_status check_grid(const srp_plan_desc *d) {
+    for (int64_t i = 0; i < d->J; ++i) {
+        const double *g = d->grid_xyz + 3 * i;
+        if (!finite3(g)) return fail(SRP_ERR_INVALID_ARG, "grid_xyz not finite");
+        if (d->grid_kind == SRP_GRID_DIRECTIONS) {
+            const double n = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            if (fabs(n - 1.0) > 1e-6)
+                return fail(SRP_ERR_INVALID_ARG, "direction vectors must have unit length");
+        }
+    }
+    return SRP_OK;
+}
+
+void fill_info(const Layout &lay, srp_plan_info *info) {
+    info->M = lay.M;
+    info->Q = lay.Q;
+    info->K = lay.K;
+    info->Kb = lay.Kb;
+    info->J = lay.J;
+    info->n_aux = lay.n_aux;
+    info->S = lay.S;
+    info->max_nq = lay.max_nq;
+    info->x_frac_bits = lay.xf;
+    info->max_frames = lay.L_max;
+    info->device_bytes = lay.total();
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+
+void release(srp_plan_s *h) {
+    cudaFree(h->d_pairs);
+    cudaFree(h->d_nq);
+    cudaFree(h->d_off);
+    cudaFree(h->d_x);
+    cudaFree(h->d_twid);
+    cudaFree(h->d_psi);
+    cudaFree(h->d_xi);
+    cudaFree(h->d_xi16);
+    cudaFree(h->d_part);
+    cudaFree(h->d_in_stage);
+    cudaFree(h->d_maps_stage);
+    cudaFree(h->d_argmax_stage);
+    cudaFree(h->d_peak_stage);
+    for (auto &e : h->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+// Build the TDOA table in FP64 (Eq. Deltat_i / Eq. Deltat_i_spher), convert
+// x = Delta t fs to fixed point and upload it as [Q][J_pad].
+srp_status build_tdoa(const srp_plan_desc *d, srp_plan_s *h) {
+    const Layout &lay = h->lay;
+    std::vector<int32_t> X((size_t)lay.Q * lay.J_pad, 0);
+    const double scale = ldexp(1.0, lay.xf);
+    const bool far = d->grid_kind == SRP_GRID_DIRECTIONS;
+    for (int64_t i = 0; i < lay.J; ++i) {
+        const double *g = d->grid_xyz + 3 * i;
+        double dist[kMaxM];
+        if (!far)
+            for (int m = 0; m < lay.M; ++m) {
+                const double *p = d->mic_xyz + 3 * m;
+                const double dx = p[0] - g[0], dy = p[1] - g[1], dz = p[2] - g[2];
+                dist[m] = sqrt(dx * dx + dy * dy + dz * dz);
+            }
+        for (int q = 0; q < lay.Q; ++q) {
+            const int m = lay.pm[q], mp = lay.pmp[q];
+            double dt;
+            if (far) {
+                const double *a = d->mic_xyz + 3 * m, *b = d->mic_xyz + 3 * mp;
+                dt = ((a[0] - b[0]) * g[0] + (a[1] - b[1]) * g[1] + (a[2] - b[2]) * g[2]) / d->c;
+            } else {
+                dt = (dist[m] - dist[mp]) / d->c;
+            }
+            X[(size_t)q * lay.J_pad + i] = (int32_t)llround(dt * d->fs * scale);
+        }
+    }
+    SRP_CUDA(cudaMemcpy(h->d_x, X.data(), lay.b_x, cudaMemcpyHostToDevice), "upload TDOA table");
+    return SRP_OK;
+}
+
+srp_status check_handle(srp_handle h) {
+    if (h == nullptr) return fail(SRP_ERR_INVALID_ARG, "handle is NULL");
+    return SRP_OK;
+}
+
+void record(srp_plan_s *h, int idx, cudaStream_t s) {
+    if (h->timing) cudaEventRecord(h->ev[idx], s);
+}
+
+// The hot path: K1 (STFT input) -> K2 + K3 (Nyquist) or K4 (conventional) -> K5.
+srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_t *d_argmax,
+                   float *d_peak, cudaStream_t s) {
+    const Layout &lay = h->lay;
+    int launches = 0;
+    for (int &r : h->stage_ran) r = 0;
+    record(h, 0, s);
+    const float2 *psi = static_cast<const float2 *>(d_in);
+    if (h->input_kind == SRP_IN_STFT) {
+        SRP_CUDA(launch_phat(static_cast<const float2 *>(d_in), L, lay.M, lay.Kb, h->d_pairs,
+                             lay.Q, h->d_psi, s), "PHAT kernel");
+        psi = h->d_psi;
+        h->stage_ran[kStagePhat] = 1;
+        ++launches;
+    }
+    record(h, 1, s);
+    if (h->mode == SRP_MODE_NYQUIST) {
+        SRP_CUDA(launch_gcc_samples(psi, L, lay.Q, lay.K, h->d_nq, h->d_off, lay.n_aux, h->d_twid,
+                                    h->d_xi, lay.L_pad, 1, s), "GCC sample kernel");
+        h->stage_ran[kStageGcc] = 1;
+        ++launches;
+    }
+    record(h, 2, s);
+    if (h->mode == SRP_MODE_NYQUIST) {
+        SRP_CUDA(launch_interp_simt(h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq, h->d_off, lay.n_aux,
+                                    lay.xf, h->d_xi, lay.L_pad, L, d_maps, h->d_part, lay.n_tiles,
+                                    s), "interpolation kernel");
+    } else {
+        SRP_CUDA(launch_conv_simt(h->d_x, lay.J_pad, lay.J, lay.Q, lay.K, lay.xf, psi, L, d_maps,
+                                  h->d_part, lay.n_tiles, s), "conventional kernel");
+    }
+    h->stage_ran[kStageMap] = 1;
+    ++launches;
+    record(h, 3, s);
+    SRP_CUDA(launch_argmax(h->d_part, lay.n_tiles, L, d_argmax, d_peak, s), "argmax kernel");
+    h->stage_ran[kStageArgmax] = 1;
+    ++launches;
+    record(h, 4, s);
+    h->last_launches = launches;
+    return SRP_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+}  // namespace srp
+
+using namespace srp;
+
+extern "C" {
+
+srp_status srp_plan_describe(const srp_plan_desc *d, srp_plan_info *info, int32_t *Nq_out) {
+    Layout lay;
+    srp_status st = make_layout(d, lay);
+    if (st != SRP_OK) return st;
+    if (info != nullptr) fill_info(lay, info);
+    if (Nq_out != nullptr) memcpy(Nq_out, lay.Nq.data(), sizeof(int32_t) * lay.Q);
+    return SRP_OK;
+}
+
+srp_status srp_plan_footprint(const srp_plan_desc *d, size_t *device_bytes) {
+    if (device_bytes == nullptr) return fail(SRP_ERR_INVALID_ARG, "device_bytes is NULL");
+    Layout lay;
+    srp_status st = make_layout(d, lay);
+    if (st != SRP_OK) return st;
+    *device_bytes = lay.total();
+    return SRP_OK;
+}
+
+srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
+    if (out == nullptr) return fail(SRP_ERR_INVALID_ARG, "out is NULL");
+    Layout lay;
+    srp_status st = make_layout(d, lay);
+    if (st != SRP_OK) return st;
+    if ((st = check_grid(d)) != SRP_OK) return st;
+    if (d->precision != SRP_PREC_FP32)
+        return fail(SRP_ERR_UNSUPPORTED, "BF16/FP16 contractions are not built in this library");
+    srp_plan_s *h = new (std::nothrow) srp_plan_s();
+    if (h == nullptr) return fail(SRP_ERR_OOM, "host allocation failed");
+    h->lay = std::move(lay);
+    h->mode = d->mode;
+    h->precision = d->precision;
+    h->input_kind = d->input_kind;
+    h->host_io = d->host_io;
+    const Layout &L = h->lay;
+    auto bail = [&](srp_status s) {
+        release(h);
+        delete h;
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+#define SRP_ALLOC(ptr, bytes)                                            \
+    do {                                                                 \
+        cudaError_t e_ = dalloc(&(ptr), (bytes));                        \
+        if (e_ != cudaSuccess) return bail(cuda_fail(e_, "cudaMalloc")); \
+    } while (0)
+    SRP_ALLOC(h->d_pairs, L.b_pairs);
+    SRP_ALLOC(h->d_nq, L.b_nq);
+    SRP_ALLOC(h->d_off, L.b_off);
+    SRP_ALLOC(h->d_x, L.b_x);
+    SRP_ALLOC(h->d_twid, L.b_twid);
+    SRP_ALLOC(h->d_psi, L.b_psi);
+    SRP_ALLOC(h->d_xi, L.b_xi);
+    SRP_ALLOC(h->d_xi16, L.b_xi16);
+    SRP_ALLOC(h->d_part, L.b_part);
+    if (h->host_io) {
+        SRP_ALLOC(h->d_in_stage, L.b_in_stage);
+        SRP_ALLOC(h->d_maps_stage, L.b_maps_stage);
+        SRP_ALLOC(h->d_argmax_stage, L.b_small_stage / 2);
+        SRP_ALLOC(h->d_peak_stage, L.b_small_stage / 2);
+    }
+#undef SRP_ALLOC
+    std::vector<int2> pairs(L.Q);
+    for (int q = 0; q < L.Q; ++q) pairs[q] = make_int2(L.pm[q], L.pmp[q]);
+    auto up = [&](void *dst, const void *src, size_t n) -> cudaError_t {
+        return n ? cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    if ((e = up(h->d_pairs, pairs.data(), L.b_pairs)) != cudaSuccess ||
+        (e = up(h->d_nq, L.Nq.data(), L.b_nq)) != cudaSuccess ||
+        (e = up(h->d_off, L.off.data(), L.b_off)) != cudaSuccess)
+        return bail(cuda_fail(e, "upload pair tables"));
+    if (L.b_twid) {
+        std::vector<float2> tw(L.K);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int j = 0; j < L.K; ++j)
+            tw[j] = make_float2((float)cos(two_pi * j / L.K), (float)sin(two_pi * j / L.K));
+        if ((e = up(h->d_twid, tw.data(), L.b_twid)) != cudaSuccess)
+            return bail(cuda_fail(e, "upload twiddles"));
+    }
+    // Padding rows and frames of the GCC-sample buffers stay zero for ever.
+    if (L.b_xi && (e = cudaMemset(h->d_xi, 0, L.b_xi)) != cudaSuccess)
+        return bail(cuda_fail(e, "clear GCC buffer"));
+    if (L.b_xi16 && (e = cudaMemset(h->d_xi16, 0, L.b_xi16)) != cudaSuccess)
+        return bail(cuda_fail(e, "clear GCC buffer"));
+    if ((st = build_tdoa(d, h)) != SRP_OK) return bail(st);
+    for (auto &ev : h->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail(e, "plan upload"));
+    *out = h;
+    return SRP_OK;
+}
+
+srp_status srp_plan_get_info(srp_handle h, srp_plan_info *info) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (info == nullptr) return fail(SRP_ERR_INVALID_ARG, "info is NULL");
+    fill_info(h->lay, info);
+    return SRP_OK;
+}
+
+srp_status srp_plan_tdoa(srp_handle h, double *x_host) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (x_host == nullptr) return fail(SRP_ERR_INVALID_ARG, "x_host is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
+    const Layout &L = h->lay;
+    std::vector<int32_t> X((size_t)L.Q * L.J_pad);
+    SRP_CUDA(cudaMemcpy(X.data(), h->d_x, L.b_x, cudaMemcpyDeviceToHost), "download TDOA table");
+    const double inv = ldexp(1.0, -L.xf);
+    for (int64_t i = 0; i < L.J; ++i)
+        for (int q = 0; q < L.Q; ++q) x_host[i * L.Q + q] = X[(size_t)q * L.J_pad + i] * inv;
+    return SRP_OK;
+}
+
+srp_status srp_map(srp_handle h, const void *d_in, int32_t L, float *d_maps, int32_t *d_argmax,
+                   float *d_peak, srp_stream_t s) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (L < 0 || L > h->lay.L_max) return fail(SRP_ERR_INVALID_ARG, "L out of [0, max_frames]");
+    if (L == 0) return SRP_OK;
+    if (d_in == nullptr || d_argmax == nullptr)
+        return fail(SRP_ERR_INVALID_ARG, "d_in and d_argmax must be non-NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
+    return run_map(h, d_in, L, d_maps, d_argmax, d_peak, reinterpret_cast<cudaStream_t>(s));
+}
+
+srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps,
+                        int32_t *h_argmax, float *h_peak, srp_stream_t s) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (!h->host_io) return fail(SRP_ERR_INVALID_ARG, "plan was built without host_io");
+    if (L < 0 || L > h->lay.L_max) return fail(SRP_ERR_INVALID_ARG, "L out of [0, max_frames]");
+    if (L == 0) return SRP_OK;
+    if (h_in == nullptr || h_argmax == nullptr)
+        return fail(SRP_ERR_INVALID_ARG, "h_in and h_argmax must be non-NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+    const Layout &lay = h->lay;
+    const int rows = h->input_kind == SRP_IN_STFT ? lay.M : lay.Q;
+    const size_t in_bytes = sizeof(float2) * (size_t)L * rows * lay.Kb;
+    SRP_CUDA(cudaMemcpyAsync(h->d_in_stage, h_in, in_bytes, cudaMemcpyHostToDevice, cs),
+             "copy input to device");
+    st = run_map(h, h->d_in_stage, L, h_maps ? h->d_maps_stage : nullptr, h->d_argmax_stage,
+                 h->d_peak_stage, cs);
+    if (st != SRP_OK) return st;
+    if (h_maps)
+        SRP_CUDA(cudaMemcpyAsync(h_maps, h->d_maps_stage, sizeof(float) * (size_t)L * lay.J,
+                                 cudaMemcpyDeviceToHost, cs), "copy maps to host");
+    SRP_CUDA(cudaMemcpyAsync(h_argmax, h->d_argmax_stage, sizeof(int32_t) * L,
+                             cudaMemcpyDeviceToHost, cs), "copy argmax to host");
+    if (h_peak)
+        SRP_CUDA(cudaMemcpyAsync(h_peak, h->d_peak_stage, sizeof(float) * L,
+                                 cudaMemcpyDeviceToHost, cs), "copy peak to host");
+    SRP_CUDA(cudaStreamSynchronize(cs), "synchronise stream");
+    return SRP_OK;
+}
+
+srp_status srp_cross_spectra(srp_handle h, const void *d_y, int32_t L, void *d_psi,
+                             srp_stream_t s) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (h->input_kind != SRP_IN_STFT) return fail(SRP_ERR_INVALID_ARG, "plan takes cross spectra");
+    if (L < 0 || L > h->lay.L_max) return fail(SRP_ERR_INVALID_ARG, "L out of [0, max_frames]");
+    if (L == 0) return SRP_OK;
+    if (d_y == nullptr || d_psi == nullptr) return fail(SRP_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
+    const Layout &lay = h->lay;
+    SRP_CUDA(launch_phat(static_cast<const float2 *>(d_y), L, lay.M, lay.Kb, h->d_pairs, lay.Q,
+                         static_cast<float2 *>(d_psi), reinterpret_cast<cudaStream_t>(s)),
+             "PHAT kernel");
+    return SRP_OK;
+}
+
+srp_status srp_gcc_samples(srp_handle h, const void *d_in, int32_t L, float *d_xi,
+                           srp_stream_t s) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (h->mode != SRP_MODE_NYQUIST) return fail(SRP_ERR_INVALID_ARG, "plan is conventional");
+    if (L < 0 || L > h->lay.L_max) return fail(SRP_ERR_INVALID_ARG, "L out of [0, max_frames]");
+    if (L == 0) return SRP_OK;
+    if (d_in == nullptr || d_xi == nullptr) return fail(SRP_ERR_INVALID_ARG, "NULL buffer");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
+    const Layout &lay = h->lay;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+    const float2 *psi = static_cast<const float2 *>(d_in);
+    if (h->input_kind == SRP_IN_STFT) {
+        SRP_CUDA(launch_phat(psi, L, lay.M, lay.Kb, h->d_pairs, lay.Q, h->d_psi, cs),
+                 "PHAT kernel");
+        psi = h->d_psi;
+    }
+    SRP_CUDA(launch_gcc_samples(psi, L, lay.Q, lay.K, h->d_nq, h->d_off, lay.n_aux, h->d_twid,
+                                d_xi, 1, lay.S, cs), "GCC sample kernel");
+    return SRP_OK;
+}
+
+srp_status srp_set_timing(srp_handle h, int32_t enable) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    h->timing = enable != 0;
+    return SRP_OK;
+}
+
+srp_status srp_stage_times(srp_handle h, float *ms, int32_t n) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (ms == nullptr || n < 0) return fail(SRP_ERR_INVALID_ARG, "bad output buffer");
+    if (!h->timing) return fail(SRP_ERR_INVALID_ARG, "timing is disabled");
+    DeviceGuard g(h->device);
+    SRP_CUDA(cudaEventSynchronize(h->ev[kNumStages]), "wait for timing events");
+    for (int k = 0; k < n; ++k) {
+        ms[k] = 0.0f;
+        if (k < kNumStages && h->stage_ran[k])
+            SRP_CUDA(cudaEventElapsedTime(&ms[k], h->ev[k], h->ev[k + 1]), "event elapsed time");
+    }
+    return SRP_OK;
+}
+
+srp_status srp_last_launch_count(srp_handle h, int32_t *n) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (n == nullptr) return fail(SRP_ERR_INVALID_ARG, "n is NULL");
+    *n = h->last_launches;
+    return SRP_OK;
+}
+
+srp_status srp_destroy(srp_handle h) {
+    if (h == nullptr) return SRP_OK;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    release(h);
+    delete h;
+    return SRP_OK;
+}
+
+const char *srp_status_string(srp_status s) {
+    switch (s) {
+        case SRP_OK: return "ok";
+        case SRP_ERR_INVALID_ARG: return "invalid argument";
+        case SRP_ERR_OOM: return "out of memory";
+        case SRP_ERR_CUDA: return "CUDA error";
+        case SRP_ERR_UNSUPPORTED: return "unsupported";
+        case SRP_ERR_TIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+const char *srp_last_error_message(void) { return g_err.c_str(); }
+
+}  // extern "C"

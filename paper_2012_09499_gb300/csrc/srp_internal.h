@@ -1,0 +1,91 @@
+// Internal declarations shared by the host planner (srp_api.cu) and the
+// kernels (srp_kernels.cu, srp_tc.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/srp.h"
+
+namespace srp {
+
+// Candidate tile of every map kernel: one CTA owns 128 consecutive candidates.
+constexpr int kTileJ = 128;
+// Frame granularity of the GCC-sample buffer (rows of xi are padded to it).
+constexpr int kFramePad = 16;
+// Lag granularity of the GCC-sample buffer (the tensor-core K step).
+constexpr int kLagPad = 64;
+// Stages reported by srp_stage_times.
+enum Stage { kStagePhat = 0, kStageGcc = 1, kStageMap = 2, kStageArgmax = 3, kNumStages = 4 };
+
+// Host-side sizes of a plan; shared by describe / footprint / plan.
+struct Layout {
+    int M = 0, Q = 0, K = 0, Kb = 0, n_aux = 0, S = 0, S_pad = 0, max_nq = 0, xf = 0;
+    int64_t J = 0, J_pad = 0;
+    int L_max = 0, L_pad = 0, n_tiles = 0;
+    std::vector<int32_t> Nq, off, pm, pmp;  // per pair
+    // byte counts of every device buffer, in allocation order
+    size_t b_pairs = 0, b_nq = 0, b_off = 0, b_x = 0, b_twid = 0, b_psi = 0, b_xi = 0,
+           b_xi16 = 0, b_part = 0, b_in_stage = 0, b_maps_stage = 0, b_small_stage = 0;
+    size_t total() const {
+        return b_pairs + b_nq + b_off + b_x + b_twid + b_psi + b_xi + b_xi16 + b_part +
+               b_in_stage + b_maps_stage + b_small_stage;
+    }
+};
+
+}  // namespace srp
+
+struct srp_plan_s {
+    int device = 0;
+    srp_mode mode = SRP_MODE_NYQUIST;
+    srp_precision precision = SRP_PREC_FP32;
+    srp_input_kind input_kind = SRP_IN_STFT;
+    int host_io = 0;
+    srp::Layout lay;
+    // device tables (owned)
+    int2 *d_pairs = nullptr;       // [Q] (m, m')
+    int32_t *d_nq = nullptr;       // [Q] N_q
+    int32_t *d_off = nullptr;      // [Q] first GCC-sample row of pair q
+    int32_t *d_x = nullptr;        // [Q][J_pad] TDOA in samples, fixed point with xf fraction bits
+    float2 *d_twid = nullptr;      // [K] (cos, sin)(2 pi j / K)
+    // scratch (owned)
+    float2 *d_psi = nullptr;       // [L_max][Q][Kb] cross spectra (STFT input only)
+    float *d_xi = nullptr;         // [S_pad][L_pad] GCC samples, frames contiguous
+    uint16_t *d_xi16 = nullptr;    // [L_pad][S_pad] GCC samples as bf16/fp16, lags contiguous
+    unsigned long long *d_part = nullptr;  // [L_pad][n_tiles] per-tile argmax keys
+    // staging for srp_map_host (owned, optional)
+    void *d_in_stage = nullptr;
+    float *d_maps_stage = nullptr;
+    int32_t *d_argmax_stage = nullptr;
+    float *d_peak_stage = nullptr;
+    // timing
+    int timing = 0;
+    cudaEvent_t ev[srp::kNumStages + 1] = {};
+    int stage_ran[srp::kNumStages] = {};
+    int last_launches = 0;
+};
+
+namespace srp {
+
+void set_error(const std::string &msg);
+
+// ---- kernel launchers (srp_kernels.cu); each returns cudaGetLastError() ----
+cudaError_t launch_phat(const float2 *y, int L, int M, int Kb, const int2 *pairs, int Q,
+                        float2 *psi, cudaStream_t s);
+cudaError_t launch_gcc_samples(const float2 *psi, int L, int Q, int K, const int32_t *nq,
+                               const int32_t *off, int n_aux, const float2 *twid, float *xi,
+                               int64_t s_stride, int64_t l_stride, cudaStream_t s);
+cudaError_t launch_interp_simt(const int32_t *x, int64_t J_pad, int64_t J, int Q,
+                               const int32_t *nq, const int32_t *off, int n_aux, int xf,
+                               const float *xi, int L_pad, int L, float *maps,
+                               unsigned long long *part, int n_tiles, cudaStream_t s);
+cudaError_t launch_conv_simt(const int32_t *x, int64_t J_pad, int64_t J, int Q, int K, int xf,
+                             const float2 *psi, int L, float *maps, unsigned long long *part,
+                             int n_tiles, cudaStream_t s);
+cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,
+                          float *peak, cudaStream_t s);
+
+}  // namespace srp

@@ -1,0 +1,251 @@
+"""Python binding of the SRP C ABI (``include/srp.h``).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of ``libsrp.so``.  The functions keep the C names; tensors are torch
+CUDA tensors passed by ``data_ptr()``; streams default to torch's current
+stream.  There is no CPU fallback: loading fails loudly if the library has
+not been built (``python -m paper_2012_09499_gb300.build_lib``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsrp.so")
+
+SRP_OK, SRP_ERR_INVALID_ARG, SRP_ERR_OOM, SRP_ERR_CUDA, SRP_ERR_UNSUPPORTED, SRP_ERR_TIMEOUT = range(6)
+MODES = {"conventional": 1, "nyquist": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+INPUTS = {"stft": 0, "cross": 1}
+STAGES = ("cross_spectra", "gcc_samples", "map", "argmax")
+
+
+class SrpError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class srp_plan_desc(ctypes.Structure):
+    _fields_ = [
+        ("M", ctypes.c_int32), ("mic_xyz", ctypes.POINTER(ctypes.c_double)),
+        ("grid_kind", ctypes.c_int), ("J", ctypes.c_int64),
+        ("grid_xyz", ctypes.POINTER(ctypes.c_double)),
+        ("fs", ctypes.c_double), ("c", ctypes.c_double), ("K", ctypes.c_int32),
+        ("mode", ctypes.c_int), ("n_aux", ctypes.c_int32), ("precision", ctypes.c_int),
+        ("input_kind", ctypes.c_int), ("max_frames", ctypes.c_int32),
+        ("host_io", ctypes.c_int32),
+    ]
+
+
+class srp_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("M", ctypes.c_int32), ("Q", ctypes.c_int32), ("K", ctypes.c_int32),
+        ("Kb", ctypes.c_int32), ("J", ctypes.c_int64), ("n_aux", ctypes.c_int32),
+        ("S", ctypes.c_int32), ("max_nq", ctypes.c_int32), ("x_frac_bits", ctypes.c_int32),
+        ("max_frames", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libsrp.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2012_09499_gb300.build_lib`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
+        dp = ctypes.POINTER(srp_plan_desc)
+        sigs = {
+            "srp_plan_describe": [dp, ctypes.POINTER(srp_plan_info), vp],
+            "srp_plan_footprint": [dp, ctypes.POINTER(ctypes.c_size_t)],
+            "srp_plan": [dp, ctypes.POINTER(vp)],
+            "srp_plan_get_info": [vp, ctypes.POINTER(srp_plan_info)],
+            "srp_plan_tdoa": [vp, vp],
+            "srp_map": [vp, vp, i32, vp, vp, vp, vp],
+            "srp_map_host": [vp, vp, i32, vp, vp, vp, vp],
+            "srp_cross_spectra": [vp, vp, i32, vp, vp],
+            "srp_gcc_samples": [vp, vp, i32, vp, vp],
+            "srp_set_timing": [vp, i32],
+            "srp_stage_times": [vp, vp, i32],
+            "srp_last_launch_count": [vp, ctypes.POINTER(i32)],
+            "srp_destroy": [vp],
+        }
+        for name, args in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = st
+        L.srp_status_string.argtypes = [st]
+        L.srp_status_string.restype = ctypes.c_char_p
+        L.srp_last_error_message.argtypes = []
+        L.srp_last_error_message.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != SRP_OK:
+        L = lib()
+        detail = (L.srp_status_string(status) or b"").decode()
+        msg = (L.srp_last_error_message() or b"").decode()
+        raise SrpError(status, where, f"{detail}: {msg}" if msg else detail)
+
+
+def _ptr(t):
+    """Device address of a tensor (or None for NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _host_ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="fp32",
+              input_kind="stft", max_frames=64, far_field=False, host_io=False):
+    """Fill an srp_plan_desc; returns (desc, keep-alive arrays)."""
+    mic = np.ascontiguousarray(mic_xyz, np.float64)
+    grid = np.ascontiguousarray(grid_xyz, np.float64)
+    d = srp_plan_desc()
+    d.M = mic.shape[0]
+    d.mic_xyz = mic.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.grid_kind = 1 if far_field else 0
+    d.J = grid.shape[0]
+    d.grid_xyz = grid.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.fs, d.c, d.K = float(fs), float(c), int(K)
+    d.mode = MODES[mode]
+    d.n_aux = int(n_aux)
+    d.precision = PRECISIONS[precision]
+    d.input_kind = INPUTS[input_kind]
+    d.max_frames = int(max_frames)
+    d.host_io = 1 if host_io else 0
+    return d, (mic, grid)
+
+
+def srp_plan_describe(desc):
+    info = srp_plan_info()
+    nq = np.zeros(max(desc.M * (desc.M - 1) // 2, 1), np.int32)
+    _check(lib().srp_plan_describe(ctypes.byref(desc), ctypes.byref(info), nq.ctypes.data),
+           "srp_plan_describe")
+    return info, nq[: info.Q]
+
+
+def srp_plan_footprint(desc) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().srp_plan_footprint(ctypes.byref(desc), ctypes.byref(b)), "srp_plan_footprint")
+    return int(b.value)
+
+
+def srp_plan(desc):
+    h = ctypes.c_void_p()
+    _check(lib().srp_plan(ctypes.byref(desc), ctypes.byref(h)), "srp_plan")
+    return h
+
+
+def srp_plan_get_info(h):
+    info = srp_plan_info()
+    _check(lib().srp_plan_get_info(h, ctypes.byref(info)), "srp_plan_get_info")
+    return info
+
+
+def srp_plan_tdoa(h):
+    info = srp_plan_get_info(h)
+    x = np.zeros((info.J, info.Q), np.float64)
+    _check(lib().srp_plan_tdoa(h, x.ctypes.data), "srp_plan_tdoa")
+    return x
+
+
+def srp_map(h, d_in, L, d_maps, d_argmax, d_peak=None, stream=None):
+    _check(lib().srp_map(h, _ptr(d_in), int(L), _ptr(d_maps), _ptr(d_argmax), _ptr(d_peak),
+                         _stream(stream)), "srp_map")
+
+
+def srp_map_host(h, h_in, L, h_maps, h_argmax, h_peak=None, stream=None):
+    _check(lib().srp_map_host(h, _host_ptr(h_in), int(L), _host_ptr(h_maps),
+                              _host_ptr(h_argmax), _host_ptr(h_peak), _stream(stream)),
+           "srp_map_host")
+
+
+def srp_cross_spectra(h, d_y, L, d_psi, stream=None):
+    _check(lib().srp_cross_spectra(h, _ptr(d_y), int(L), _ptr(d_psi), _stream(stream)),
+           "srp_cross_spectra")
+
+
+def srp_gcc_samples(h, d_in, L, d_xi, stream=None):
+    _check(lib().srp_gcc_samples(h, _ptr(d_in), int(L), _ptr(d_xi), _stream(stream)),
+           "srp_gcc_samples")
+
+
+def srp_set_timing(h, enable=True):
+    _check(lib().srp_set_timing(h, 1 if enable else 0), "srp_set_timing")
+
+
+def srp_stage_times(h):
+    ms = (ctypes.c_float * len(STAGES))()
+    _check(lib().srp_stage_times(h, ctypes.addressof(ms), len(STAGES)), "srp_stage_times")
+    return dict(zip(STAGES, list(ms)))
+
+
+def srp_last_launch_count(h) -> int:
+    n = ctypes.c_int32()
+    _check(lib().srp_last_launch_count(h, ctypes.byref(n)), "srp_last_launch_count")
+    return int(n.value)
+
+
+def srp_destroy(h):
+    _check(lib().srp_destroy(h), "srp_destroy")
+
+
+class Plan:
+    """Owns one plan handle; allocates outputs with torch for convenience."""
+
+    def __init__(self, mic_xyz, grid_xyz, fs, c, K, **kw):
+        self.desc, self._keep = make_desc(mic_xyz, grid_xyz, fs, c, K, **kw)
+        self.handle = srp_plan(self.desc)
+        self.info = srp_plan_get_info(self.handle)
+
+    def map(self, d_in, L=None, maps=True, stream=None):
+        """Run the hot path on a complex64 CUDA tensor ([L][M][Kb] STFT or
+        [L][Q][Kb] cross spectra); returns (maps[L][J] or None, argmax[L], peak[L])."""
+        import torch
+        L = d_in.shape[0] if L is None else L
+        dev = d_in.device
+        out_maps = torch.empty((L, self.info.J), dtype=torch.float32, device=dev) if maps else None
+        am = torch.empty(L, dtype=torch.int32, device=dev)
+        pk = torch.empty(L, dtype=torch.float32, device=dev)
+        srp_map(self.handle, d_in, L, out_maps, am, pk, stream)
+        return out_maps, am, pk
+
+    def close(self):
+        if self.handle is not None:
+            srp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,129 @@
+"""The C ABI without a GPU: the library loads, exports every declared entry
+point, and its host-only planner (validation, pair table, lag counts, sizes)
+agrees with the oracle and the paper's worked example."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2012_09499_gb300 import build_lib, srp, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build_lib.build()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names |= set(re.findall(r"^SRP_API\s+[\w\s\*]+?\b(srp_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(srp.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings():
+    L = srp.lib()
+    assert L.srp_status_string(0) == b"ok"
+    assert L.srp_status_string(5) == b"timeout"
+    assert L.srp_destroy(None) == 0
+
+
+def _desc(**kw):
+    rng = np.random.default_rng(kw.pop("seed", 0))
+    mic = kw.pop("mic", rng.uniform(-0.25, 0.25, (kw.pop("M", 6), 3)))
+    grid = kw.pop("grid", rng.uniform(-2, 2, (kw.pop("J", 100), 3)))
+    base = dict(fs=16000.0, c=343.0, K=512)
+    base.update({k: kw.pop(k) for k in list(kw) if k in base})
+    return srp.make_desc(mic, grid, base["fs"], base["c"], base["K"], **kw)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_describe_matches_oracle_lag_counts(seed):
+    rng = np.random.default_rng(100 + seed)
+    M = int(rng.integers(2, 17))
+    mic = rng.uniform(-0.5, 0.5, (M, 3))
+    n_aux = int(rng.integers(0, 4))
+    d, keep = srp.make_desc(mic, np.zeros((3, 3)), 16000.0, 343.0, 1024, n_aux=n_aux)
+    info, nq = srp.srp_plan_describe(d)
+    ref, _ = oracle.lag_counts(mic, 16000.0, 343.0)
+    assert nq.tolist() == ref.tolist()
+    assert info.Q == M * (M - 1) // 2
+    assert info.S == int(np.sum(2 * ref + 2 * n_aux + 1))
+    assert info.max_nq == int(ref.max())
+
+
+def test_describe_paper_example():
+    """Sec. 4 array: N_q in {4 (x6), 8 (x6), 9 (x3)}, so S = 2*99 + 15(2 N_aux + 1)."""
+    mic = synth.circular_array(6, 0.1)
+    dirs = synth.half_sphere_directions(2.0)
+    for n_aux in range(4):
+        d, keep = srp.make_desc(mic, dirs, 16000.0, 340.0, 2048, n_aux=n_aux, far_field=True)
+        info, nq = srp.srp_plan_describe(d)
+        assert sorted(nq.tolist()) == [4] * 6 + [8] * 6 + [9] * 3
+        assert info.S == 198 + 15 * (2 * n_aux + 1)
+        assert info.J == 8101
+
+
+def test_exact_integer_lag_bound():
+    mic = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])
+    d, keep = srp.make_desc(mic, np.zeros((1, 3)), 8192.0, 256.0, 64)
+    _, nq = srp.srp_plan_describe(d)
+    assert nq.tolist() == [16]
+
+
+def test_footprint_counts_every_buffer():
+    d, keep = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2)
+    info, nq = srp.srp_plan_describe(d)
+    fp = srp.srp_plan_footprint(d)
+    assert fp == info.device_bytes
+    Q, Jp, Lp = 28, 1024, 64
+    Sp = -(-info.S // 64) * 64
+    expect = (8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 1024 + 8 * 64 * Q * 513
+              + 4 * Sp * Lp + 8 * Lp * (Jp // 128))
+    assert fp == expect
+    d2, keep2 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional")
+    fp2 = srp.srp_plan_footprint(d2)
+    assert fp2 == 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("M", 1), ("M", 65), ("K", 7), ("K", 2), ("K", 16384), ("J", 0), ("fs", 0.0),
+    ("c", -1.0), ("n_aux", -1), ("max_frames", 0), ("mode", 3), ("precision", 7),
+    ("input_kind", 5), ("grid_kind", 4),
+])
+def test_invalid_descriptors_rejected(field, value):
+    d, keep = _desc()
+    setattr(d, field, value)
+    with pytest.raises(srp.SrpError) as e:
+        srp.srp_plan_describe(d)
+    assert e.value.status == srp.SRP_ERR_INVALID_ARG
+
+
+def test_nonfinite_geometry_rejected():
+    mic = np.zeros((3, 3))
+    mic[1, 0] = np.nan
+    d, keep = srp.make_desc(mic, np.zeros((4, 3)), 16000.0, 343.0, 64)
+    with pytest.raises(srp.SrpError) as e:
+        srp.srp_plan_describe(d)
+    assert e.value.status == srp.SRP_ERR_INVALID_ARG
+
+
+def test_null_handle_rejected():
+    with pytest.raises(srp.SrpError) as e:
+        srp.srp_map(None, 1, 1, None, 1, stream=0)
+    assert e.value.status == srp.SRP_ERR_INVALID_ARG

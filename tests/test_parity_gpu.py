@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance for the FP32 path: max_i |map - oracle| <= 1e-4 x max_i |oracle|
+per frame; argmax equal to the oracle's first maximiser except on documented
+ties (the oracle's value at the GPU's index within twice that bound of the
+oracle's maximum).  The GPU's argmax must also be the exact first maximiser
+of the GPU's own map, and its peak the exact map value there.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2012_09499_gb300 import build_lib, srp, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build_lib.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_run(mic, grid, fs, c, K, Y, mode, n_aux=2, far=False, input_kind="stft",
+            max_frames=None, L=None, maps=True, precision="fp32"):
+    L = Y.shape[0] if L is None else L
+    plan = srp.Plan(mic, grid, fs, c, K, mode=mode, n_aux=n_aux, far_field=far,
+                    input_kind=input_kind, max_frames=max_frames or max(L, 1),
+                    precision=precision)
+    m, a, p = plan.map(dev(Y[:L]), L=L, maps=maps)
+    torch.cuda.synchronize()
+    out = (None if m is None else m.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy())
+    plan.close()
+    return out
+
+
+def check_self_consistent(maps, idx, peak):
+    L = maps.shape[0]
+    assert np.array_equal(idx, np.argmax(maps, axis=1))
+    assert np.array_equal(peak, maps[np.arange(L), idx])
+
+
+def check_against_oracle(maps, idx, ref, tol):
+    peak = np.abs(ref).max(axis=1)
+    err = np.abs(maps.astype(np.float64) - ref).max(axis=1)
+    assert np.all(err <= tol * peak), (err / peak).max()
+    ridx = np.argmax(ref, axis=1)
+    for l in np.nonzero(idx != ridx)[0]:  # documented ties only
+        gap = ref[l, ridx[l]] - ref[l, idx[l]]
+        assert gap <= 2 * tol * peak[l], (l, gap / peak[l])
+    return (err / peak).max()
+
+
+def oracle_maps(cfg, mode, n_aux=2, Y=None, far=False):
+    Y = cfg["Y"] if Y is None else Y
+    maps, _, _ = oracle.srp_map(Y, cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"],
+                                mode=mode, n_aux=n_aux, far_field=far)
+    return maps
+
+
+# --------------------------------------------------------------------------
+# stage by stage
+# --------------------------------------------------------------------------
+
+def test_cross_spectra_match_oracle():
+    cfg = synth.tiny_2d(seed=1, L=8)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], max_frames=8)
+    L, Q, Kb = 8, 6, cfg["K"] // 2 + 1
+    psi = torch.empty((L, Q, Kb), dtype=torch.complex64, device="cuda")
+    srp.srp_cross_spectra(plan.handle, dev(cfg["Y"]), L, psi)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(psi.cpu().numpy(), oracle.phat(cfg["Y"]), atol=2e-6)
+
+
+@pytest.mark.parametrize("n_aux", [0, 3])
+def test_gcc_samples_match_oracle(n_aux):
+    cfg = synth.room_3d(seed=2, L=5, shape=(4, 4, 4), spacing=1.0)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], n_aux=n_aux,
+                    max_frames=7)
+    S = plan.info.S
+    xi = torch.full((5, S), float("nan"), dtype=torch.float32, device="cuda")
+    srp.srp_gcc_samples(plan.handle, dev(cfg["Y"]), 5, xi)
+    torch.cuda.synchronize()
+    Nq, _ = oracle.lag_counts(cfg["mic"], cfg["fs"], cfg["c"])
+    ref = oracle.gcc_samples(oracle.phat(cfg["Y"]), Nq, n_aux, cfg["K"])
+    np.testing.assert_allclose(xi.cpu().numpy(), ref, atol=3e-6)
+
+
+@pytest.mark.parametrize("far", [False, True])
+def test_plan_tdoa_matches_oracle(far):
+    rng = np.random.default_rng(3)
+    mic = rng.uniform(-0.3, 0.3, (7, 3))
+    if far:
+        grid = synth.half_sphere_directions(4.0)
+    else:
+        grid = rng.uniform(-3, 3, (777, 3))
+    plan = srp.Plan(mic, grid, 16000.0, 343.0, 256, far_field=far)
+    x = srp.srp_plan_tdoa(plan.handle)
+    ref = oracle.tdoa(mic, grid, 16000.0, 343.0, far_field=far)
+    assert np.abs(x - ref).max() <= 2.0 ** -(plan.info.x_frac_bits + 1) + 1e-12
+
+
+# --------------------------------------------------------------------------
+# whole path
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode,n_aux", [("nyquist", 2), ("nyquist", 0), ("conventional", 0)])
+def test_map_tiny_2d(mode, n_aux):
+    """2D square array, 41 x 41 grid, K = 512, L = 16 (several tiles, ragged tail)."""
+    for seed in (0, 1):
+        cfg = synth.tiny_2d(seed=seed, L=16)
+        maps, idx, peak = gpu_run(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"],
+                                  cfg["Y"], mode, n_aux)
+        check_self_consistent(maps, idx, peak)
+        check_against_oracle(maps, idx, oracle_maps(cfg, mode, n_aux), TOL_FP32)
+
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+def test_map_far_field_half_sphere(mode):
+    """The paper's evaluation geometry (Sec. 4): M = 6 circle, r = 10 cm,
+    lower half sphere at 2 degrees (J = 8101), far field."""
+    rng = np.random.default_rng(4)
+    mic = synth.circular_array(6, 0.1)
+    dirs = synth.half_sphere_directions(2.0)
+    Y = synth.free_field_stft(rng, mic, [dirs[3000]], 16000.0, 512, 6, 10.0, c=340.0,
+                              far_field=True)
+    cfg = dict(mic=mic, grid=dirs, fs=16000.0, c=340.0, K=512, Y=Y)
+    maps, idx, peak = gpu_run(mic, dirs, 16000.0, 340.0, 512, Y, mode, 2, far=True)
+    check_self_consistent(maps, idx, peak)
+    check_against_oracle(maps, idx, oracle_maps(cfg, mode, 2, far=True), TOL_FP32)
+
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+def test_map_cross_spectra_input(mode):
+    cfg = synth.tiny_2d(seed=5, L=4)
+    psi = oracle.phat(cfg["Y"]).astype(np.complex64)
+    maps, idx, peak = gpu_run(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], psi, mode,
+                              input_kind="cross")
+    ref, _, _ = oracle.srp_map(None, cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"],
+                               mode=mode, n_aux=2, psi=psi)
+    check_self_consistent(maps, idx, peak)
+    check_against_oracle(maps, idx, ref, TOL_FP32)
+
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+def test_map_room_3d_full_size_sampled(mode):
+    """The 3D workload at full size (M = 8, J = 480000, K = 1024, L = 64) in
+    the launch configuration the benchmark times; the oracle checks sampled
+    candidates of sampled frames, including every GPU maximiser."""
+    cfg = synth.room_3d(seed=0)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], mode=mode, n_aux=2,
+                    max_frames=64)
+    m, a, p = plan.map(dev(cfg["Y"]))
+    torch.cuda.synchronize()
+    maps, idx, peak = m.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy()
+    check_self_consistent(maps, idx, peak)
+    rng = np.random.default_rng(0)
+    frames = np.array([0, 21, 63])
+    cand = np.unique(np.concatenate([rng.choice(cfg["grid"].shape[0], 3000, replace=False),
+                                     idx[frames]]))
+    x = oracle.tdoa(cfg["mic"], cfg["grid"][cand], cfg["fs"], cfg["c"])
+    psi = oracle.phat(cfg["Y"][frames])
+    if mode == "conventional":
+        ref = oracle.conventional(psi, x, cfg["K"])
+    else:
+        Nq, _ = oracle.lag_counts(cfg["mic"], cfg["fs"], cfg["c"])
+        ref = oracle.nyquist(oracle.gcc_samples(psi, Nq, 2, cfg["K"]), Nq, 2, x)
+    sub = maps[frames][:, cand].astype(np.float64)
+    peak_ref = np.abs(ref).max(axis=1)
+    assert np.all(np.abs(sub - ref).max(axis=1) <= TOL_FP32 * peak_ref)
+    # the GPU maximiser is (within tolerance) at least as high as every sampled candidate
+    at_idx = np.array([ref[r, np.searchsorted(cand, idx[f])] for r, f in enumerate(frames)])
+    assert np.all(at_idx >= ref.max(axis=1) - 2 * TOL_FP32 * peak_ref)
+
+
+def test_map_room_3d_full_frame_nyquist():
+    """One whole frame of the 3D workload against the oracle, all 480000 candidates."""
+    cfg = synth.room_3d(seed=1)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], n_aux=2,
+                    max_frames=64)
+    m, a, p = plan.map(dev(cfg["Y"]))
+    torch.cuda.synchronize()
+    maps, idx = m.cpu().numpy(), a.cpu().numpy()
+    x = oracle.tdoa(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"])
+    psi = oracle.phat(cfg["Y"][:1])
+    Nq, _ = oracle.lag_counts(cfg["mic"], cfg["fs"], cfg["c"])
+    ref = oracle.nyquist(oracle.gcc_samples(psi, Nq, 2, cfg["K"]), Nq, 2, x)
+    check_against_oracle(maps[:1], idx[:1], ref, TOL_FP32)
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+@pytest.mark.parametrize("J,L,max_frames", [(1, 1, 1), (129, 3, 5), (300, 37, 40), (257, 17, 17)])
+def test_ragged_sizes(mode, J, L, max_frames):
+    rng = np.random.default_rng(J + L)
+    mic = rng.uniform(-0.2, 0.2, (3, 3))
+    grid = rng.uniform(-2, 2, (J, 3))
+    Y = synth.free_field_stft(rng, mic, [np.array([1.0, 0.5, 0.2])], 16000.0, 64, L, 5.0)
+    maps, idx, peak = gpu_run(mic, grid, 16000.0, 343.0, 64, Y, mode, 1, max_frames=max_frames)
+    cfg = dict(mic=mic, grid=grid, fs=16000.0, c=343.0, K=64, Y=Y)
+    check_self_consistent(maps, idx, peak)
+    check_against_oracle(maps, idx, oracle_maps(cfg, mode, 1), TOL_FP32)
+
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+def test_two_mics_small_K(mode):
+    rng = np.random.default_rng(6)
+    mic = np.array([[-0.05, 0.0, 0.0], [0.05, 0.0, 0.0]])
+    grid = rng.uniform(-1, 1, (200, 3))
+    Y = synth.free_field_stft(rng, mic, [np.array([0.7, 0.3, 0.0])], 16000.0, 16, 4, 30.0)
+    maps, idx, peak = gpu_run(mic, grid, 16000.0, 343.0, 16, Y, mode, 0)
+    cfg = dict(mic=mic, grid=grid, fs=16000.0, c=343.0, K=16, Y=Y)
+    check_against_oracle(maps, idx, oracle_maps(cfg, mode, 0), TOL_FP32)
+
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+def test_integer_tdoas(mode):
+    """Broadside (x = 0) and end-fire (x = +-16 exactly: d = 0.5 m, c = 256,
+    fs = 8192) candidates take the exact-sample branch of the interpolation."""
+    mic = np.array([[-0.25, 0.0, 0.0], [0.25, 0.0, 0.0]])
+    grid = np.array([[0.0, 1.0, 0.0], [0.0, -2.0, 0.5], [3.0, 0.0, 0.0], [-1.0, 0.0, 0.0],
+                     [0.4, 0.9, 0.0], [0.0, 0.3, 0.0]])
+    rng = np.random.default_rng(7)
+    Y = synth.free_field_stft(rng, mic, [np.array([1.0, 1.0, 0.0])], 8192.0, 128, 3, 20.0,
+                              c=256.0)
+    cfg = dict(mic=mic, grid=grid, fs=8192.0, c=256.0, K=128, Y=Y)
+    x = oracle.tdoa(mic, grid, 8192.0, 256.0)
+    assert x[0, 0] == 0.0 and x[2, 0] == -16.0 and x[3, 0] == 16.0
+    maps, idx, peak = gpu_run(mic, grid, 8192.0, 256.0, 128, Y, mode, 2)
+    check_against_oracle(maps, idx, oracle_maps(cfg, mode, 2), TOL_FP32)
+
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+def test_zero_input_ties_to_first_candidate(mode):
+    cfg = synth.tiny_2d(seed=0, L=3)
+    Y = np.zeros_like(cfg["Y"])
+    maps, idx, peak = gpu_run(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], Y, mode)
+    assert np.all(maps == 0.0) and np.all(idx == 0) and np.all(peak == 0.0)
+
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+def test_without_maps_and_host_entry_agree(mode):
+    cfg = synth.tiny_2d(seed=2, L=9)
+    args = (cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"])
+    maps, idx, peak = gpu_run(*args, cfg["Y"], mode)
+    _, idx2, peak2 = gpu_run(*args, cfg["Y"], mode, maps=False)
+    assert np.array_equal(idx, idx2) and np.array_equal(peak, peak2)
+    plan = srp.Plan(*args, mode=mode, max_frames=9, host_io=True)
+    hm = np.zeros((9, cfg["grid"].shape[0]), np.float32)
+    ha = np.zeros(9, np.int32)
+    hp = np.zeros(9, np.float32)
+    srp.srp_map_host(plan.handle, cfg["Y"], 9, hm, ha, hp)
+    assert np.array_equal(hm, maps) and np.array_equal(ha, idx) and np.array_equal(hp, peak)
+
+
+def test_deterministic_and_timed():
+    cfg = synth.tiny_2d(seed=3, L=16)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], max_frames=16)
+    srp.srp_set_timing(plan.handle, True)
+    Y = dev(cfg["Y"])
+    m1, a1, _ = plan.map(Y)
+    t = srp.srp_stage_times(plan.handle)
+    m2, a2, _ = plan.map(Y)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m2) and torch.equal(a1, a2)
+    assert srp.srp_last_launch_count(plan.handle) == 4
+    assert all(v > 0 for v in t.values())
+
+
+def test_frame_count_limits():
+    cfg = synth.tiny_2d(seed=0, L=4)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], max_frames=4)
+    Y = dev(cfg["Y"])
+    out = torch.empty((4, plan.info.J), device="cuda")
+    am = torch.empty(4, dtype=torch.int32, device="cuda")
+    srp.srp_map(plan.handle, Y, 0, out, am)  # L = 0 is a no-op
+    with pytest.raises(srp.SrpError) as e:
+        srp.srp_map(plan.handle, Y, 5, out, am)
+    assert e.value.status == srp.SRP_ERR_INVALID_ARG
