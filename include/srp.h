@@ -170,6 +170,31 @@ SRP_API srp_status srp_cross_spectra(srp_handle h, const void *d_y, int32_t L, v
 SRP_API srp_status srp_gcc_samples(srp_handle h, const void *d_in, int32_t L, float *d_xi,
                            srp_stream_t s);
 
+/* srp_gcc_samples without a plan and without any device allocation.  The
+ * paper has no counterpart: this entry exists for callers that may not call
+ * cudaMalloc, e.g. code inside a host application whose device allocator is
+ * owned by someone else, or a real-time audio thread that must not block on
+ * the allocator.  Everything a plan would allocate is replaced:
+ *  - the cross spectra between the two kernels go to one file-scope device
+ *    array of 8 MiB, which every GPU that loads this library holds until the
+ *    process exits; L * Q * (K/2+1) * 8 bytes must fit in it, else the call
+ *    returns SRP_ERR_INVALID_ARG and launches nothing;
+ *  - the pair table travels as a kernel argument, so M <= 16;
+ *  - twiddles are generated on the device.
+ * Inputs: M and K as in srp_plan_desc, n_aux >= 0, Nq host [Q] lag counts
+ * (for example from srp_plan_describe, which is host-only), d_y device
+ * y[L][M][Kb] complex64.  Output: d_xi device float [L][S], exactly as
+ * srp_gcc_samples writes it.  Asynchronous on s.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and every call
+ * overwrites the part it reads, so nothing carries over between calls, but
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * on it: order them.                                                     */
+SRP_API srp_status srp_gcc_samples_static(int32_t M, int32_t K, int32_t n_aux,
+                                          const int32_t *Nq, const void *d_y, int32_t L,
+                                          float *d_xi, srp_stream_t s);
+
 /* Per-stage timing: when enabled, srp_map records CUDA events around each
  * stage on its stream; srp_stage_times waits for the last call's events and
  * returns milliseconds per stage in ms[0..n): 0 cross spectra, 1 GCC

@@ -249,3 +249,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def srp_gcc_samples_static(M, K, n_aux, Nq, d_y, L, d_xi, stream=None):
+    """srp_gcc_samples without a plan or any device allocation (scratch in a
+    fixed 8 MiB device array inside the library); Nq is a host int32 [Q]."""
+    fn = lib().srp_gcc_samples_static
+    fn.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    nq = np.ascontiguousarray(Nq, np.int32)
+    _check(fn(int(M), int(K), int(n_aux), nq.ctypes.data, _ptr(d_y), int(L), _ptr(d_xi),
+              _stream(stream)), "srp_gcc_samples_static")
