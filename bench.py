@@ -188,6 +188,16 @@ def time_steps(step, steps, warmup, flush, stream, world, timed_stage=None):
     return ms, np.array(stage_ms), wall
 
 
+def measured_bf16_peak():
+    """Dense BF16 TFLOP/s measured on this machine (burst), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "of fallback"
+
+
 def bench_ours(args):
     import torch
 
@@ -265,8 +275,25 @@ def bench_ours(args):
     cv_ms = reduce_max(res["conventional"]["ms"].mean(), world, dev if world > 1 else None)
     k3_ms = float(np.mean(res["nyquist"]["stage"]))
     flops = 2.0 * J * S * L  # multiply-adds of the interpolation contraction, C_int x L
-    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12  # CUDA-core FP32 FMA rate at the max SM clock
     achieved = flops / (k3_ms * 1e-3) / 1e12
+    bf16_peak, peak_src = measured_bf16_peak()
+    # FP32 accuracy is three BF16 products per multiply-add, so its peak is a third
+    split_peak = bf16_peak / 3.0
+
+    # reduced-precision variants of the same step (Nyquist, tensor cores)
+    variants = {}
+    for prec in ("bf16", "fp16"):
+        pl = srp.Plan(mic, grid, w["fs"], 343.0, w["K"], mode="nyquist", n_aux=w["n_aux"],
+                      max_frames=L, precision=prec)
+        srp.srp_set_timing(pl.handle, True)
+        ms_v, st_v, _ = time_steps(make_step(pl), max(3, min(args.steps, 20)), args.warmup,
+                                   flush, stream, world, stage_time(pl))
+        variants[prec] = {"ms_per_step": float(ms_v.mean()),
+                          "value": world * J * Q * L / (float(ms_v.mean()) * 1e-3),
+                          "map_ms": float(st_v.mean()),
+                          "map_frac_of_bf16_peak": flops / (float(st_v.mean()) * 1e-3) / 1e12
+                          / bf16_peak}
+        pl.close()
 
     if rank != 0:
         return
@@ -291,12 +318,14 @@ def bench_ours(args):
         "map_error_bound": "FP32 path: max |map - FP64 oracle| <= 1e-4 x peak (tests)",
         "stage_ms": {k: v for k, v in srp.srp_stage_times(plans["conventional"].handle).items()},
         "roofline": {
-            "kernel": "k_interp_simt (sinc interpolation + pair sum, FP32 CUDA cores)",
-            "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
-            "algorithmic": f"2*J*S*L = {flops:.4g} flop per launch; {k3_ms:.4f} ms per launch",
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts x max clock)",
+            "kernel": "k_interp_tc<split> (sinc interpolation + pair sum, tcgen05, FP32 as 3 BF16 products)",
+            "bound": "tensor", "achieved": achieved, "peak": split_peak, "unit": "TFLOP/s",
+            "frac": achieved / split_peak, "traffic": None,
+            "algorithmic": f"2*J*S*L = {flops:.4g} flop per launch (S={S} lags); "
+                           f"{k3_ms:.4f} ms per launch",
+            "peak_source": f"measured bf16 {bf16_peak:.1f} TFLOP/s ({peak_src}) / 3 products",
         },
+        "precision_variants": variants,
         "e2e": {"value": world * cells / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
                 "h2d_bytes_per_step": int(L * w["M"] * (w["K"] // 2 + 1) * 8),
                 "d2h_bytes_per_step": int(L * J * 4 + L * 8),

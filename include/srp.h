@@ -88,6 +88,11 @@ typedef enum {
     SRP_IN_CROSS = 1 /* input psi[L][Q][Kb] complex64 cross spectra, already weighted */
 } srp_input_kind;
 
+typedef enum {
+    SRP_ENGINE_AUTO = 0,      /* tensor cores (tcgen05) where built, else CUDA cores */
+    SRP_ENGINE_CUDA_CORES = 1 /* FP32 CUDA-core kernels only (FP32 precision) */
+} srp_engine;
+
 typedef struct {
     int32_t M;                /* microphones, 2 <= M <= 64 */
     const double *mic_xyz;    /* host [M][3] metres; copied by srp_plan */
@@ -103,6 +108,7 @@ typedef struct {
     srp_input_kind input_kind;/* STFT frames or ready cross spectra */
     int32_t max_frames;       /* largest L a call may pass, >= 1 */
     int32_t host_io;          /* nonzero: also size staging buffers for srp_map_host */
+    srp_engine engine;        /* which units run the map contraction */
 } srp_plan_desc;
 
 /* Sizes of a plan, computed on the host (no device needed). */
@@ -194,6 +200,13 @@ SRP_API srp_status srp_gcc_samples(srp_handle h, const void *d_in, int32_t L, fl
 SRP_API srp_status srp_gcc_samples_static(int32_t M, int32_t K, int32_t n_aux,
                                           const int32_t *Nq, const void *d_y, int32_t L,
                                           float *d_xi, srp_stream_t s);
+
+/* Device error flags raised since the previous poll, read on stream s
+ * (which is synchronised) and cleared.  Returns SRP_ERR_TIMEOUT if a
+ * bounded wait inside a tensor-core kernel gave up (the kernel then
+ * returned early and its outputs are invalid), else SRP_OK.  srp_map_host
+ * polls by itself.                                                        */
+SRP_API srp_status srp_poll_device_status(srp_handle h, srp_stream_t s);
 
 /* Per-stage timing: when enabled, srp_map records CUDA events around each
  * stage on its stream; srp_stage_times waits for the last call's events and

@@ -82,6 +82,8 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         return fail(SRP_ERR_INVALID_ARG, "unknown input kind");
     if (d->grid_kind != SRP_GRID_POINTS && d->grid_kind != SRP_GRID_DIRECTIONS)
         return fail(SRP_ERR_INVALID_ARG, "unknown grid kind");
+    if (d->engine != SRP_ENGINE_AUTO && d->engine != SRP_ENGINE_CUDA_CORES)
+        return fail(SRP_ERR_INVALID_ARG, "unknown engine");
     if (d->max_frames < 1 || d->max_frames > kMaxFrames)
         return fail(SRP_ERR_INVALID_ARG, "max_frames must be in [1, 65536]");
     for (int m = 0; m < d->M; ++m)
@@ -128,6 +130,22 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     }
     lay.S = (int)S;
     lay.S_pad = (int)round_up(S, kLagPad);
+    // The Nyquist map runs on the tensor cores unless CUDA cores are asked
+    // for; the conventional map and the CUDA-core engine are FP32 only.
+    lay.tc = d->mode == SRP_MODE_NYQUIST && d->engine == SRP_ENGINE_AUTO;
+    if (!lay.tc && d->precision != SRP_PREC_FP32)
+        return fail(SRP_ERR_UNSUPPORTED,
+                    "BF16/FP16 need the Nyquist mode on the tensor-core engine");
+    if (lay.tc) {
+        int64_t s8 = 0;
+        for (int q = 0; q < lay.Q; ++q) {
+            lay.off8.push_back((int32_t)s8);
+            s8 += round_up(2 * (int64_t)lay.Nq[q] + 2 * (int64_t)d->n_aux + 1, 8);
+        }
+        lay.S8 = (int)s8;
+        lay.S8_pad = (int)round_up(s8, kLagPad);
+        lay.N_tc = interp_tc_frames_per_cta(d->max_frames);
+    }
 
     // Fixed-point TDOA: the largest xf <= 24 with (max|x| + 2) 2^xf < 2^31.
     // Far-field directions must be unit vectors so that |x| <= d fs / c.
@@ -146,8 +164,10 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     lay.b_twid = nyq ? sizeof(float2) * lay.K : 0;
     lay.b_psi = d->input_kind == SRP_IN_STFT
                     ? sizeof(float2) * (size_t)lay.L_max * lay.Q * lay.Kb : 0;
-    lay.b_xi = nyq ? sizeof(float) * (size_t)lay.S_pad * lay.L_pad : 0;
-    lay.b_xi16 = (nyq && half) ? sizeof(uint16_t) * (size_t)lay.S_pad * lay.L_pad : 0;
+    lay.b_xi = (nyq && !lay.tc) ? sizeof(float) * (size_t)lay.S_pad * lay.L_pad : 0;
+    lay.b_xi16 = lay.tc ? sizeof(uint16_t) * (half ? 1 : 2) * (size_t)lay.L_pad * lay.S8_pad : 0;
+    lay.b_off8 = lay.tc ? sizeof(int32_t) * lay.Q : 0;
+    lay.b_status = sizeof(int);
     lay.b_part = sizeof(unsigned long long) * (size_t)lay.L_pad * lay.n_tiles;
     if (d->host_io) {
         const int rows = d->input_kind == SRP_IN_STFT ? lay.M : lay.Q;
@@ -201,6 +221,8 @@ void release(srp_plan_s *h) {
     cudaFree(h->d_psi);
     cudaFree(h->d_xi);
     cudaFree(h->d_xi16);
+    cudaFree(h->d_off8);
+    cudaFree(h->d_status);
     cudaFree(h->d_part);
     cudaFree(h->d_in_stage);
     cudaFree(h->d_maps_stage);
@@ -267,14 +289,26 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
         ++launches;
     }
     record(h, 1, s);
-    if (h->mode == SRP_MODE_NYQUIST) {
+    if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
+        const int fmt = h->precision == SRP_PREC_FP32 ? 1 : (h->precision == SRP_PREC_FP16 ? 2 : 0);
+        SRP_CUDA(launch_gcc_samples_tc(psi, L, lay.Q, lay.K, h->d_nq, h->d_off8, lay.n_aux,
+                                       h->d_twid, h->d_xi16, lay.L_pad, lay.S8_pad, fmt, s),
+                 "GCC sample kernel");
+        h->stage_ran[kStageGcc] = 1;
+        ++launches;
+    } else if (h->mode == SRP_MODE_NYQUIST) {
         SRP_CUDA(launch_gcc_samples(psi, L, lay.Q, lay.K, h->d_nq, h->d_off, lay.n_aux, h->d_twid,
                                     h->d_xi, lay.L_pad, 1, s), "GCC sample kernel");
         h->stage_ran[kStageGcc] = 1;
         ++launches;
     }
     record(h, 2, s);
-    if (h->mode == SRP_MODE_NYQUIST) {
+    if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
+        SRP_CUDA(launch_interp_tc(h->xi_map, lay.N_tc, h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq,
+                                  lay.n_aux, lay.xf, lay.S8_pad, lay.L_pad, L, h->precision,
+                                  d_maps, h->d_part, lay.n_tiles, h->d_status, s),
+                 "tensor-core interpolation kernel");
+    } else if (h->mode == SRP_MODE_NYQUIST) {
         SRP_CUDA(launch_interp_simt(h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq, h->d_off, lay.n_aux,
                                     lay.xf, h->d_xi, lay.L_pad, L, d_maps, h->d_part, lay.n_tiles,
                                     s), "interpolation kernel");
@@ -327,8 +361,6 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     srp_status st = make_layout(d, lay);
     if (st != SRP_OK) return st;
     if ((st = check_grid(d)) != SRP_OK) return st;
-    if (d->precision != SRP_PREC_FP32)
-        return fail(SRP_ERR_UNSUPPORTED, "BF16/FP16 contractions are not built in this library");
     srp_plan_s *h = new (std::nothrow) srp_plan_s();
     if (h == nullptr) return fail(SRP_ERR_OOM, "host allocation failed");
     h->lay = std::move(lay);
@@ -357,6 +389,8 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     SRP_ALLOC(h->d_psi, L.b_psi);
     SRP_ALLOC(h->d_xi, L.b_xi);
     SRP_ALLOC(h->d_xi16, L.b_xi16);
+    SRP_ALLOC(h->d_off8, L.b_off8);
+    SRP_ALLOC(h->d_status, L.b_status);
     SRP_ALLOC(h->d_part, L.b_part);
     if (h->host_io) {
         SRP_ALLOC(h->d_in_stage, L.b_in_stage);
@@ -372,7 +406,9 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     };
     if ((e = up(h->d_pairs, pairs.data(), L.b_pairs)) != cudaSuccess ||
         (e = up(h->d_nq, L.Nq.data(), L.b_nq)) != cudaSuccess ||
-        (e = up(h->d_off, L.off.data(), L.b_off)) != cudaSuccess)
+        (e = up(h->d_off, L.off.data(), L.b_off)) != cudaSuccess ||
+        (e = up(h->d_off8, L.off8.data(), L.b_off8)) != cudaSuccess ||
+        (e = cudaMemset(h->d_status, 0, L.b_status)) != cudaSuccess)
         return bail(cuda_fail(e, "upload pair tables"));
     if (L.b_twid) {
         std::vector<float2> tw(L.K);
@@ -387,6 +423,11 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
         return bail(cuda_fail(e, "clear GCC buffer"));
     if (L.b_xi16 && (e = cudaMemset(h->d_xi16, 0, L.b_xi16)) != cudaSuccess)
         return bail(cuda_fail(e, "clear GCC buffer"));
+    if (L.tc) {
+        const int rows = (h->precision == SRP_PREC_FP32 ? 2 : 1) * L.L_pad;
+        if ((e = encode_xi_map(h->d_xi16, rows, L.S8_pad, L.N_tc, h->xi_map)) != cudaSuccess)
+            return bail(cuda_fail(e, "cuTensorMapEncodeTiled"));
+    }
     if ((st = build_tdoa(d, h)) != SRP_OK) return bail(st);
     for (auto &ev : h->ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
@@ -460,6 +501,21 @@ srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps
         SRP_CUDA(cudaMemcpyAsync(h_peak, h->d_peak_stage, sizeof(float) * L,
                                  cudaMemcpyDeviceToHost, cs), "copy peak to host");
     SRP_CUDA(cudaStreamSynchronize(cs), "synchronise stream");
+    return srp_poll_device_status(h, s);
+}
+
+srp_status srp_poll_device_status(srp_handle h, srp_stream_t s) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+    int flags = 0;
+    SRP_CUDA(cudaMemcpyAsync(&flags, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, cs),
+             "read device status");
+    SRP_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), cs), "clear device status");
+    SRP_CUDA(cudaStreamSynchronize(cs), "synchronise stream");
+    if (flags & 1) return fail(SRP_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel gave up");
     return SRP_OK;
 }
 

@@ -9,44 +9,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "srp_device.cuh"
 #include "srp_internal.h"
 
 namespace srp {
 namespace {
 
-constexpr float kInvPi = 0.318309886183790671537767526745f;
-
-// Key whose unsigned order is (map value ascending, candidate index
-// descending): the maximum key is the first maximiser.  -0 is folded to +0 so
-// that equal zeros tie on the index.
-__device__ __forceinline__ unsigned long long argmax_key(float v, uint32_t i) {
-    if (v == 0.0f) v = 0.0f;
-    uint32_t u = __float_as_uint(v);
-    uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    return ((unsigned long long)o << 32) | (unsigned long long)(0xFFFFFFFFu - i);
-}
-
-__device__ __forceinline__ float key_value(unsigned long long k) {
-    uint32_t o = (uint32_t)(k >> 32);
-    uint32_t u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
-    return __uint_as_float(u);
-}
-
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long t = __shfl_xor_sync(0xFFFFFFFFu, k, o);
-        k = t > k ? t : k;
-    }
-    return k;
-}
-
-// Decode a fixed-point TDOA X = round(x 2^xf) into x = x0 + f with x0 the
-// nearest integer and f in [-1/2, 1/2) exact in FP32.
-__device__ __forceinline__ void decode_tdoa(int32_t X, int xf, int &x0, float &f) {
-    x0 = (X + (1 << (xf - 1))) >> xf;
-    f = (float)(X - x0 * (1 << xf)) * __int_as_float((127 - xf) << 23);
-}
+using namespace dev;
 
 // ---------------------------------------------------------------------------
 // K1: psi_q(k) = u_m(k) conj(u_m'(k)) with u = y / |y| (0 where y = 0).  That
@@ -93,34 +62,14 @@ __global__ void __launch_bounds__(128) k_gcc_samples(
     const int32_t *__restrict__ off, int n_aux, const float2 *__restrict__ twid,
     float *__restrict__ xi, int64_t s_stride, int64_t l_stride) {
     extern __shared__ float2 sm[];
-    const int Kb = K / 2 + 1;
     float2 *tw = sm, *ps = sm + K;
     const int q = blockIdx.x, l = blockIdx.y;
-    for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = twid[j];
-    const float2 *row = psi + ((size_t)l * Q + q) * Kb;
-    for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
-        const float2 v = row[k];
-        const float a = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
-        ps[k] = make_float2(a * v.x, a * v.y);
-    }
+    stage_gcc_row(psi + ((size_t)l * Q + q) * (K / 2 + 1), twid, K, tw, ps);
     __syncthreads();
-    const int nmax = nq[q] + n_aux, base = off[q];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const float inv_k = 1.0f / (float)K;
-    for (int t = warp; t <= 2 * nmax; t += nw) {
-        const int n = t - nmax;
-        const int nm = ((n % K) + K) % K;
-        float acc = 0.0f;
-        for (int k = lane; k < Kb; k += 32) {
-            const float2 w = tw[(k * nm) % K];
-            const float2 p = ps[k];
-            acc = fmaf(p.x, w.x, acc);
-            acc = fmaf(-p.y, w.y, acc);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-        if (lane == 0) xi[(int64_t)(base + t) * s_stride + (int64_t)l * l_stride] = acc * inv_k;
-    }
+    const int base = off[q];
+    gcc_row(tw, ps, K, nq[q] + n_aux, [&](int t, int, float v) {
+        xi[(int64_t)(base + t) * s_stride + (int64_t)l * l_stride] = v;
+    });
 }
 
 // Shared epilogue of the map kernels: write the tile's maps (if requested)

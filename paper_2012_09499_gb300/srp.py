@@ -20,6 +20,7 @@ SRP_OK, SRP_ERR_INVALID_ARG, SRP_ERR_OOM, SRP_ERR_CUDA, SRP_ERR_UNSUPPORTED, SRP
 MODES = {"conventional": 1, "nyquist": 2}
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 INPUTS = {"stft": 0, "cross": 1}
+ENGINES = {"auto": 0, "cuda_cores": 1}
 STAGES = ("cross_spectra", "gcc_samples", "map", "argmax")
 
 
@@ -37,7 +38,7 @@ class srp_plan_desc(ctypes.Structure):
         ("fs", ctypes.c_double), ("c", ctypes.c_double), ("K", ctypes.c_int32),
         ("mode", ctypes.c_int), ("n_aux", ctypes.c_int32), ("precision", ctypes.c_int),
         ("input_kind", ctypes.c_int), ("max_frames", ctypes.c_int32),
-        ("host_io", ctypes.c_int32),
+        ("host_io", ctypes.c_int32), ("engine", ctypes.c_int),
     ]
 
 
@@ -77,6 +78,7 @@ def lib():
             "srp_stage_times": [vp, vp, i32],
             "srp_last_launch_count": [vp, ctypes.POINTER(i32)],
             "srp_destroy": [vp],
+            "srp_poll_device_status": [vp, vp],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -125,7 +127,7 @@ def _stream(s):
 
 
 def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="fp32",
-              input_kind="stft", max_frames=64, far_field=False, host_io=False):
+              input_kind="stft", max_frames=64, far_field=False, host_io=False, engine="auto"):
     """Fill an srp_plan_desc; returns (desc, keep-alive arrays)."""
     mic = np.ascontiguousarray(mic_xyz, np.float64)
     grid = np.ascontiguousarray(grid_xyz, np.float64)
@@ -142,6 +144,7 @@ def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="f
     d.input_kind = INPUTS[input_kind]
     d.max_frames = int(max_frames)
     d.host_io = 1 if host_io else 0
+    d.engine = ENGINES[engine]
     return d, (mic, grid)
 
 
@@ -213,6 +216,10 @@ def srp_last_launch_count(h) -> int:
     n = ctypes.c_int32()
     _check(lib().srp_last_launch_count(h, ctypes.byref(n)), "srp_last_launch_count")
     return int(n.value)
+
+
+def srp_poll_device_status(h, stream=None):
+    _check(lib().srp_poll_device_status(h, _stream(stream)), "srp_poll_device_status")
 
 
 def srp_destroy(h):

@@ -92,19 +92,25 @@ def test_footprint_counts_every_buffer():
     fp = srp.srp_plan_footprint(d)
     assert fp == info.device_bytes
     Q, Jp, Lp = 28, 1024, 64
+    S8 = int(np.sum(-(-(2 * nq + 5) // 8) * 8))
+    S8p = -(-S8 // 64) * 64
+    common = 4 + 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
+    # tensor-core engine: twiddles, 8-aligned pair offsets, split 16-bit GCC samples
+    assert fp == common + 8 * 1024 + 4 * Q + 2 * 2 * Lp * S8p
+    d3, keep3 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, engine="cuda_cores")
     Sp = -(-info.S // 64) * 64
-    expect = (8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 1024 + 8 * 64 * Q * 513
-              + 4 * Sp * Lp + 8 * Lp * (Jp // 128))
-    assert fp == expect
+    assert srp.srp_plan_footprint(d3) == common + 8 * 1024 + 4 * Sp * Lp
+    d4, keep4 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision="bf16")
+    assert srp.srp_plan_footprint(d4) == common + 8 * 1024 + 4 * Q + 2 * Lp * S8p
     d2, keep2 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional")
     fp2 = srp.srp_plan_footprint(d2)
-    assert fp2 == 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
+    assert fp2 == 4 + 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
 
 
 @pytest.mark.parametrize("field,value", [
     ("M", 1), ("M", 65), ("K", 7), ("K", 2), ("K", 16384), ("J", 0), ("fs", 0.0),
     ("c", -1.0), ("n_aux", -1), ("max_frames", 0), ("mode", 3), ("precision", 7),
-    ("input_kind", 5), ("grid_kind", 4),
+    ("input_kind", 5), ("grid_kind", 4), ("engine", 2),
 ])
 def test_invalid_descriptors_rejected(field, value):
     d, keep = _desc()
@@ -112,6 +118,15 @@ def test_invalid_descriptors_rejected(field, value):
     with pytest.raises(srp.SrpError) as e:
         srp.srp_plan_describe(d)
     assert e.value.status == srp.SRP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kw", [dict(mode="conventional", precision="bf16"),
+                                dict(engine="cuda_cores", precision="fp16")])
+def test_half_precision_needs_tensor_core_nyquist(kw):
+    d, keep = _desc(**kw)
+    with pytest.raises(srp.SrpError) as e:
+        srp.srp_plan_describe(d)
+    assert e.value.status == srp.SRP_ERR_UNSUPPORTED
 
 
 def test_nonfinite_geometry_rejected():
