@@ -137,13 +137,13 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         return fail(SRP_ERR_UNSUPPORTED,
                     "BF16/FP16 need the Nyquist mode on the tensor-core engine");
     if (lay.tc) {
-        int64_t s8 = 0;
+        int64_t sc = 0;
         for (int q = 0; q < lay.Q; ++q) {
-            lay.off8.push_back((int32_t)s8);
-            s8 += round_up(2 * (int64_t)lay.Nq[q] + 2 * (int64_t)d->n_aux + 1, 8);
+            lay.offc.push_back((int32_t)sc);
+            sc += round_up(2 * (int64_t)lay.Nq[q] + 2 * (int64_t)d->n_aux + 1, kLagPad);
         }
-        lay.S8 = (int)s8;
-        lay.S8_pad = (int)round_up(s8, kLagPad);
+        lay.Sc = (int)sc;
+        lay.n_chunks = (int)(sc / kLagPad);
         lay.N_tc = interp_tc_frames_per_cta(d->max_frames);
     }
 
@@ -165,8 +165,10 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     lay.b_psi = d->input_kind == SRP_IN_STFT
                     ? sizeof(float2) * (size_t)lay.L_max * lay.Q * lay.Kb : 0;
     lay.b_xi = (nyq && !lay.tc) ? sizeof(float) * (size_t)lay.S_pad * lay.L_pad : 0;
-    lay.b_xi16 = lay.tc ? sizeof(uint16_t) * (half ? 1 : 2) * (size_t)lay.L_pad * lay.S8_pad : 0;
-    lay.b_off8 = lay.tc ? sizeof(int32_t) * lay.Q : 0;
+    lay.b_xi16 = lay.tc ? sizeof(uint16_t) * (half ? 1 : 2) * (size_t)lay.L_pad * lay.Sc : 0;
+    lay.b_offc = lay.tc ? sizeof(int32_t) * lay.Q : 0;
+    lay.b_xs = lay.tc ? sizeof(int2) * (size_t)lay.Q * (size_t)lay.J_pad : 0;
+    lay.b_ctab = lay.tc ? sizeof(int4) * (size_t)lay.n_chunks : 0;
     lay.b_status = sizeof(int);
     lay.b_part = sizeof(unsigned long long) * (size_t)lay.L_pad * lay.n_tiles;
     if (d->host_io) {
@@ -221,7 +223,9 @@ void release(srp_plan_s *h) {
     cudaFree(h->d_psi);
     cudaFree(h->d_xi);
     cudaFree(h->d_xi16);
-    cudaFree(h->d_off8);
+    cudaFree(h->d_offc);
+    cudaFree(h->d_xs);
+    cudaFree(h->d_ctab);
     cudaFree(h->d_status);
     cudaFree(h->d_part);
     cudaFree(h->d_in_stage);
@@ -261,6 +265,41 @@ srp_status build_tdoa(const srp_plan_desc *d, srp_plan_s *h) {
         }
     }
     SRP_CUDA(cudaMemcpy(h->d_x, X.data(), lay.b_x, cudaMemcpyHostToDevice), "upload TDOA table");
+    if (!lay.tc) return SRP_OK;
+    // Tensor-core operand table: the same fixed-point TDOA with
+    // sp = (-1)^x0 sin(pi f) / pi for x = x0 + f, decoded exactly as the
+    // kernel decodes it; f = 0 (an exact sample) is taken as 2^-40.
+    std::vector<int2> xs((size_t)lay.Q * lay.J_pad);
+    const double pi = 3.141592653589793238462643383279502884;
+    const int32_t half = 1 << (lay.xf - 1);
+    for (size_t k = 0; k < xs.size(); ++k) {
+        const int32_t Xk = X[k];
+        const int32_t x0 = (Xk + half) >> lay.xf;
+        double f = ldexp((double)(Xk - x0 * (1 << lay.xf)), -lay.xf);
+        if (f == 0.0) f = ldexp(1.0, -40);
+        float sp = (float)(sin(pi * f) / pi);
+        if (x0 & 1) sp = -sp;
+        int32_t bits;
+        memcpy(&bits, &sp, sizeof bits);
+        xs[k] = make_int2(Xk, bits);
+    }
+    SRP_CUDA(cudaMemcpy(h->d_xs, xs.data(), lay.b_xs, cudaMemcpyHostToDevice),
+             "upload tensor-core TDOA table");
+    // per chunk of 64 lag slots: pair, nmax_q - first slot (float bits), groups
+    // of 8 slots to generate (even) and 16-slot MMA steps holding lags
+    std::vector<int4> ctab(lay.n_chunks);
+    for (int q = 0; q < lay.Q; ++q) {
+        const int nmax = lay.Nq[q] + lay.n_aux, span = 2 * nmax + 1;
+        for (int c0 = 0; c0 < span; c0 += kLagPad) {
+            const float moff = (float)(nmax - c0);
+            int32_t mbits;
+            memcpy(&mbits, &moff, sizeof mbits);
+            const int nk = (std::min(kLagPad, span - c0) + 15) / 16;
+            ctab[(lay.offc[q] + c0) / kLagPad] = make_int4(q, mbits, 2 * nk, nk);
+        }
+    }
+    SRP_CUDA(cudaMemcpy(h->d_ctab, ctab.data(), lay.b_ctab, cudaMemcpyHostToDevice),
+             "upload chunk table");
     return SRP_OK;
 }
 
@@ -291,8 +330,8 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     record(h, 1, s);
     if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
         const int fmt = h->precision == SRP_PREC_FP32 ? 1 : (h->precision == SRP_PREC_FP16 ? 2 : 0);
-        SRP_CUDA(launch_gcc_samples_tc(psi, L, lay.Q, lay.K, h->d_nq, h->d_off8, lay.n_aux,
-                                       h->d_twid, h->d_xi16, lay.L_pad, lay.S8_pad, fmt, s),
+        SRP_CUDA(launch_gcc_samples_tc(psi, L, lay.Q, lay.K, h->d_nq, h->d_offc, lay.n_aux,
+                                       h->d_twid, h->d_xi16, lay.L_pad, lay.Sc, fmt, s),
                  "GCC sample kernel");
         h->stage_ran[kStageGcc] = 1;
         ++launches;
@@ -304,9 +343,9 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     }
     record(h, 2, s);
     if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
-        SRP_CUDA(launch_interp_tc(h->xi_map, lay.N_tc, h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq,
-                                  lay.n_aux, lay.xf, lay.S8_pad, lay.L_pad, L, h->precision,
-                                  d_maps, h->d_part, lay.n_tiles, h->d_status, s),
+        SRP_CUDA(launch_interp_tc(h->xi_map, lay.N_tc, h->d_xs, h->d_ctab, lay.J_pad, lay.J,
+                                  lay.Q, h->d_nq, lay.n_aux, lay.xf, lay.Sc, lay.L_pad, L,
+                                  h->precision, d_maps, h->d_part, lay.n_tiles, h->d_status, s),
                  "tensor-core interpolation kernel");
     } else if (h->mode == SRP_MODE_NYQUIST) {
         SRP_CUDA(launch_interp_simt(h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq, h->d_off, lay.n_aux,
@@ -389,7 +428,9 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     SRP_ALLOC(h->d_psi, L.b_psi);
     SRP_ALLOC(h->d_xi, L.b_xi);
     SRP_ALLOC(h->d_xi16, L.b_xi16);
-    SRP_ALLOC(h->d_off8, L.b_off8);
+    SRP_ALLOC(h->d_offc, L.b_offc);
+    SRP_ALLOC(h->d_xs, L.b_xs);
+    SRP_ALLOC(h->d_ctab, L.b_ctab);
     SRP_ALLOC(h->d_status, L.b_status);
     SRP_ALLOC(h->d_part, L.b_part);
     if (h->host_io) {
@@ -407,7 +448,7 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     if ((e = up(h->d_pairs, pairs.data(), L.b_pairs)) != cudaSuccess ||
         (e = up(h->d_nq, L.Nq.data(), L.b_nq)) != cudaSuccess ||
         (e = up(h->d_off, L.off.data(), L.b_off)) != cudaSuccess ||
-        (e = up(h->d_off8, L.off8.data(), L.b_off8)) != cudaSuccess ||
+        (e = up(h->d_offc, L.offc.data(), L.b_offc)) != cudaSuccess ||
         (e = cudaMemset(h->d_status, 0, L.b_status)) != cudaSuccess)
         return bail(cuda_fail(e, "upload pair tables"));
     if (L.b_twid) {
@@ -425,7 +466,7 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
         return bail(cuda_fail(e, "clear GCC buffer"));
     if (L.tc) {
         const int rows = (h->precision == SRP_PREC_FP32 ? 2 : 1) * L.L_pad;
-        if ((e = encode_xi_map(h->d_xi16, rows, L.S8_pad, L.N_tc, h->xi_map)) != cudaSuccess)
+        if ((e = encode_xi_map(h->d_xi16, rows, L.Sc, L.N_tc, h->xi_map)) != cudaSuccess)
             return bail(cuda_fail(e, "cuTensorMapEncodeTiled"));
     }
     if ((st = build_tdoa(d, h)) != SRP_OK) return bail(st);

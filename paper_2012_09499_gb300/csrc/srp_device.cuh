@@ -19,6 +19,13 @@ __device__ __forceinline__ unsigned long long argmax_key(float v, uint32_t i) {
     return ((unsigned long long)o << 32) | (unsigned long long)(0xFFFFFFFFu - i);
 }
 
+// The upper half of argmax_key: an unsigned value in the order of v.
+__device__ __forceinline__ uint32_t ordered_value(float v) {
+    if (v == 0.0f) v = 0.0f;
+    const uint32_t u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
 __device__ __forceinline__ float key_value(unsigned long long k) {
     uint32_t o = (uint32_t)(k >> 32);
     uint32_t u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;

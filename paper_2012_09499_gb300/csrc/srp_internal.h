@@ -27,16 +27,16 @@ struct Layout {
     int64_t J = 0, J_pad = 0;
     int L_max = 0, L_pad = 0, n_tiles = 0;
     std::vector<int32_t> Nq, off, pm, pmp;  // per pair
-    // tensor-core lag layout: pair q owns ceil(N'_q / 8) groups of 8 slots
-    int S8 = 0, S8_pad = 0, N_tc = 0;
+    // tensor-core lag layout: pair q owns ceil(N'_q / 64) chunks of 64 slots
+    int Sc = 0, n_chunks = 0, N_tc = 0;
     bool tc = false;    // the Nyquist map runs on the tensor cores
-    std::vector<int32_t> off8;
+    std::vector<int32_t> offc;
     // byte counts of every device buffer, in allocation order
-    size_t b_status = 0, b_off8 = 0;
+    size_t b_status = 0, b_offc = 0, b_xs = 0, b_ctab = 0;
     size_t b_pairs = 0, b_nq = 0, b_off = 0, b_x = 0, b_twid = 0, b_psi = 0, b_xi = 0,
            b_xi16 = 0, b_part = 0, b_in_stage = 0, b_maps_stage = 0, b_small_stage = 0;
     size_t total() const {
-        return b_status + b_off8 + b_pairs + b_nq + b_off + b_x + b_twid + b_psi + b_xi + b_xi16 + b_part +
+        return b_status + b_offc + b_xs + b_ctab + b_pairs + b_nq + b_off + b_x + b_twid + b_psi + b_xi + b_xi16 + b_part +
                b_in_stage + b_maps_stage + b_small_stage;
     }
 };
@@ -59,8 +59,10 @@ struct srp_plan_s {
     // scratch (owned)
     float2 *d_psi = nullptr;       // [L_max][Q][Kb] cross spectra (STFT input only)
     float *d_xi = nullptr;         // [S_pad][L_pad] GCC samples, frames contiguous
-    uint16_t *d_xi16 = nullptr;    // [1 or 2][L_pad][S8_pad] sign-folded GCC samples, 16-bit
-    int32_t *d_off8 = nullptr;     // [Q] first 16-bit lag slot of pair q
+    uint16_t *d_xi16 = nullptr;    // [1 or 2][L_pad][Sc] sign-folded GCC samples, 16-bit
+    int32_t *d_offc = nullptr;     // [Q] first 16-bit lag slot of pair q (a multiple of 64)
+    int2 *d_xs = nullptr;          // [Q][J_pad] (fixed-point TDOA, bits of (-1)^x0 sin(pi f)/pi)
+    int4 *d_ctab = nullptr;        // [n_chunks] (pair, bits of nmax - first slot, groups, MMA steps)
     int *d_status = nullptr;       // device error flags (bit 0: a bounded wait gave up)
     alignas(64) unsigned char xi_map[128] = {};  // CUtensorMap of d_xi16
     unsigned long long *d_part = nullptr;  // [L_pad][n_tiles] per-tile argmax keys
@@ -95,12 +97,12 @@ cudaError_t launch_conv_simt(const int32_t *x, int64_t J_pad, int64_t J, int Q, 
                              int n_tiles, cudaStream_t s);
 cudaError_t encode_xi_map(void *xi16, int rows, int S_pad, int N, void *map_out);
 cudaError_t launch_gcc_samples_tc(const float2 *psi, int L, int Q, int K, const int32_t *nq,
-                                  const int32_t *off8, int n_aux, const float2 *twid,
+                                  const int32_t *offc, int n_aux, const float2 *twid,
                                   uint16_t *xi16, int L_pad, int S_pad, int fmt, cudaStream_t s);
 int interp_tc_frames_per_cta(int L);
-cudaError_t launch_interp_tc(const void *xi_map, int N, const int32_t *x, int64_t J_pad,
-                             int64_t J, int Q, const int32_t *nq, int n_aux, int xf, int S_pad,
-                             int L_pad, int L, int precision, float *maps,
+cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const int4 *ctab,
+                             int64_t J_pad, int64_t J, int Q, const int32_t *nq, int n_aux,
+                             int xf, int S_pad, int L_pad, int L, int precision, float *maps,
                              unsigned long long *part, int n_tiles, int *status, cudaStream_t s);
 cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,
                           float *peak, cudaStream_t s);

@@ -15,10 +15,13 @@
 // evaluated as f = 2^-40, which gives the unit weight at n = x0 and weights
 // below 1e-11 elsewhere.
 //
-// Lag axis: pair q owns ceil((2(N_q+N_aux)+1)/8) groups of 8 lags (the tail
-// of the last group has B = 0), so every 16-byte shared-memory chunk of A
-// belongs to one pair.  K is walked in chunks of 64 lags (one 128-byte
-// swizzle row of 16-bit data).
+// Lag axis: pair q owns ceil((2(N_q+N_aux)+1)/64) chunks of 64 lag slots
+// (one 128-byte swizzle row of 16-bit data), so every pipeline stage holds one
+// pair; the slots past the pair's last lag have B = 0.  A plan table gives
+// each chunk its pair, its first lag, the 8-lag groups to generate and the
+// 16-lag MMA steps to issue (trailing empty steps are skipped).  The plan also
+// holds, per (pair, candidate), the fixed-point TDOA and sp = (-1)^x0
+// sin(pi f)/pi computed in FP64, so no sine is evaluated here.
 //
 // FP32 precision uses three BF16 products per step (A_hi B_hi + A_hi B_lo +
 // A_lo B_hi, hi = bf16(v), lo = bf16(v - hi)); BF16 and FP16 precision use one.
@@ -41,6 +44,9 @@ constexpr int kTmaWarp = 4, kMmaWarp = 5;
 constexpr int kChunk = 64;           // lags per pipeline stage
 constexpr uint32_t kATile = 128u * 128u;  // 128 candidates x 64 lags x 2 B
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
+constexpr int kXRing = 8;            // (TDOA, sp) prefetch ring (slots per candidate row)
+constexpr int kXAhead = kXRing - 1;  // pairs in flight ahead of the current one
+constexpr int kMtStride = 130;       // floats per frame row of the epilogue tile
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -71,11 +77,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                  : "memory");
 }
 
+// One probe of the phase; a waiting thread is suspended in hardware (not
+// spinning) until the phase completes or the hint of 20 us runs out.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, "
-        "p; }"
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000; "
+        "selp.u32 %0, 1, 0, p; }"
         : "=r"(done)
         : "r"(bar), "r"(parity)
         : "memory");
@@ -88,15 +96,13 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
                                        int *status) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer();
-    for (uint32_t it = 1;; ++it) {
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0u) {
-            if (*abort_flag) return false;
-            if (global_timer() - t0 > kWaitLimitNs) {
-                *abort_flag = 1;
-                atomicOr(status, 1);
-                return false;
-            }
+        if (*abort_flag) return false;
+        if (global_timer() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            atomicOr(status, 1);
+            return false;
         }
     }
 }
@@ -175,9 +181,53 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Packed FP32 pairs (two lanes per instruction on sm_100+).
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 upk2(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
 
@@ -200,19 +250,19 @@ __device__ __forceinline__ uint32_t pack_f16(float a, float b) {
 
 // ---------------------------------------------------------------------------
 // GCC samples as 16-bit operand B: xi'[row][slot], row = frame (hi) or
-// L_pad + frame (lo), slot = off8[q] + t, value (-1)^n xi_q(n).
+// L_pad + frame (lo), slot = offc[q] + t, value (-1)^n xi_q(n).
 // ---------------------------------------------------------------------------
 template <int kFmt>  // 0: bf16, 1: bf16 hi/lo split, 2: fp16
 __global__ void __launch_bounds__(128) k_gcc_samples_tc(
     const float2 *__restrict__ psi, int Q, int K, const int32_t *__restrict__ nq,
-    const int32_t *__restrict__ off8, int n_aux, const float2 *__restrict__ twid,
+    const int32_t *__restrict__ offc, int n_aux, const float2 *__restrict__ twid,
     uint16_t *__restrict__ xi16, int L_pad, int S_pad) {
     extern __shared__ float2 sm[];
     float2 *tw = sm, *ps = sm + K;
     const int q = blockIdx.x, l = blockIdx.y;
     stage_gcc_row(psi + ((size_t)l * Q + q) * (K / 2 + 1), twid, K, tw, ps);
     __syncthreads();
-    const int base = off8[q];
+    const int base = offc[q];
     gcc_row(tw, ps, K, nq[q] + n_aux, [&](int t, int n, float v) {
         if (n & 1) v = -v;
         const size_t hi = (size_t)l * S_pad + base + t;
@@ -234,7 +284,8 @@ __global__ void __launch_bounds__(128) k_gcc_samples_tc(
 // The contraction.
 // ---------------------------------------------------------------------------
 struct TcArgs {
-    const int32_t *x;       // [Q][J_pad] fixed-point TDOA
+    const int2 *xs;         // [Q][J_pad] (fixed-point TDOA, bits of sp)
+    const int4 *ctab;       // [n_chunks] (pair, bits of nmax_q - first lag slot, groups, MMA steps)
     int64_t J_pad, J;
     int Q;
     const int32_t *nq;      // [Q]
@@ -248,7 +299,49 @@ struct TcArgs {
     unsigned long long *part;  // [L_pad][n_tiles]
     int n_tiles;
     int *status;
+    int vec_maps;           // maps rows are 8-byte aligned (float2 stores)
 };
+
+// Weights of NG groups of 8 lags for one candidate row of the A tile(s):
+// w = sp / d with d = f + (mc - k) for lag slot k of the chunk, two lags per
+// reciprocal, written at row offset a_row with the 128-byte swizzle (chunk
+// position cc ^ sw).  With kSplit, the low part bf16(w - hi) goes to the tile
+// kATile bytes further on.
+template <int NG, bool kSplit, bool kHalf>
+__device__ __forceinline__ void gen_groups(uint32_t a_row, uint32_t sw, float f, float mc,
+                                           float sp) {
+    const uint64_t f2 = pk2(f, f);
+    const uint64_t two = pk2(2.0f, 2.0f);
+    // m2 = (mc - k - 1, mc - k): the second lag of a pair first, so that
+    // (db, da) * rr = (w_a, w_b) comes out in lag order
+    uint64_t m2 = pk2(mc - 1.0f, mc);
+#pragma unroll
+    for (int cc = 0; cc < NG; ++cc) {
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint64_t d2 = add2(f2, m2);  // (db, da), each rounded once
+            m2 = sub2(m2, two);
+            const float2 d = upk2(d2);
+            const float rr = sp * rcp_approx(d.x * d.y);
+            const float2 w = upk2(mul2(d2, pk2(rr, rr)));  // (w_a, w_b)
+            if (kHalf) {
+                hv[e] = pack_f16(w.x, w.y);
+            } else {
+                hv[e] = pack_bf16(w.x, w.y);
+                if (kSplit) {
+                    const uint64_t h2 = pk2(__uint_as_float(hv[e] << 16),
+                                            __uint_as_float(hv[e] & 0xFFFF0000u));
+                    const float2 lo = upk2(sub2(pk2(w.x, w.y), h2));
+                    lv[e] = pack_bf16(lo.x, lo.y);
+                }
+            }
+        }
+        const uint32_t off = a_row + (((uint32_t)cc ^ sw) << 4);
+        st_shared_v4(off, hv[0], hv[1], hv[2], hv[3]);
+        if (kSplit) st_shared_v4(off + kATile, lv[0], lv[1], lv[2], lv[3]);
+    }
+}
 
 template <bool kSplit, bool kHalf>
 __global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
@@ -264,8 +357,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant
     const uint32_t b_tile = (uint32_t)a.N * 128u;
     const uint32_t stage_bytes = (kSplit ? 2u : 1u) * (kATile + b_tile);
     const uint32_t stage0 = base + 1024u;
-    unsigned long long *red =
-        reinterpret_cast<unsigned long long *>(gbase + 1024u + stage_bytes * (uint32_t)a.stages);
+    // per-row ring of prefetched (TDOA, sp): xring[slot][row], 8 bytes each
+    const uint32_t xring = base + 1024u + stage_bytes * (uint32_t)a.stages;
+    // epilogue tile mt[frame][kMtStride] over the (then idle) stage buffers
+    float *mt = reinterpret_cast<float *>(gbase + 1024u);
 
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
     auto empty_bar = [&](int s) { return smem_u32(&bars[4 + s]); };
@@ -298,104 +393,121 @@ __global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant
         const int r = threadIdx.x;
         const int64_t i = (int64_t)blockIdx.x * 128 + r;
         const uint32_t row = (uint32_t)r * 128u, sw = (uint32_t)(r & 7);
-        int q = -1, g_next = 0;
-        // d = f + (mg - e) for lag e of the current group: mg is an exact
-        // integer in FP32, so d is rounded once and is never 0 unless f is.
-        float sp = 0.0f, f = 0.5f, mg = 0.0f;
-        int32_t x_next = __ldg(&a.x[i]);
-        int nmax_next = __ldg(&a.nq[0]) + a.n_aux;
+        // d = f + (m - e) for lag e of a group, where m = x0 + nmax - (first lag
+        // slot of the group) is an exact integer in FP32: d is rounded once and
+        // is never 0 unless f is.
+        int q = -1;
+        float sp = 0.0f, f = 0.5f, x0f = 0.0f;
+        // (TDOA, sp) of the first kXAhead pairs start streaming in now; pair p
+        // sits in slot p % kXRing.  Pair q + 1 is read from its slot when pair q
+        // starts, one chunk or more ahead of its use, and that read issues the
+        // load of pair q + 1 + kXAhead (one commit group per pair).
+#pragma unroll
+        for (int k = 0; k < kXAhead; ++k) {
+            if (k < a.Q)
+                cp_async8(xring + (uint32_t)(k * 128 + r) * 8u, &a.xs[(size_t)k * a.J_pad + i]);
+            cp_async_commit();
+        }
+        int32_t nX, nsp;  // (TDOA, sp) of the next pair to start
+        auto read_ring = [&](int p) {
+            cp_async_wait<kXAhead - 1>();  // pair p has landed
+            asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];"
+                         : "=r"(nX), "=r"(nsp)
+                         : "r"(xring + (uint32_t)((p % kXRing) * 128 + r) * 8u));
+            const int pn = p + kXAhead;
+            if (pn < a.Q)
+                cp_async8(xring + (uint32_t)((pn % kXRing) * 128 + r) * 8u,
+                          &a.xs[(size_t)pn * a.J_pad + i]);
+            cp_async_commit();
+        };
+        read_ring(0);
+        int4 cur = __ldg(&a.ctab[0]);
         for (int c = 0; c < a.n_chunks; ++c) {
             const int st = c % a.stages;
             const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
+            const int4 nxt = __ldg(&a.ctab[c + 1 < a.n_chunks ? c + 1 : c]);
+            if (cur.x != q) {  // uniform: a new pair starts with this chunk
+                q = cur.x;
+                int x0;
+                decode_tdoa(nX, a.xf, x0, f);
+                if (f == 0.0f) f = 9.094947017729282e-13f;  // 2^-40, as in the plan
+                sp = __int_as_float(nsp);
+                x0f = (float)x0;
+                if (q + 1 < a.Q) read_ring(q + 1);
+            }
+            const float mc = x0f + __int_as_float(cur.y);  // x0 + nmax - first lag slot
+            const int ng = cur.z;
             if (c >= a.stages) mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status);
-#pragma unroll 1
-            for (int cc = 0; cc < 8; ++cc) {
-                const int g = c * 8 + cc;
-                if (g == g_next) {  // uniform: the next pair starts at this group
-                    ++q;
-                    if (q < a.Q) {
-                        int x0;
-                        decode_tdoa(x_next, a.xf, x0, f);
-                        if (f == 0.0f) f = 9.094947017729282e-13f;  // 2^-40
-                        sp = sinpif(f) * kInvPi;
-                        if (x0 & 1) sp = -sp;
-                        const int nmax = nmax_next;
-                        mg = (float)(x0 + nmax);  // d - f at n = -nmax
-                        g_next = g + (2 * nmax + 1 + 7) / 8;
-                        if (q + 1 < a.Q) {
-                            x_next = __ldg(&a.x[(size_t)(q + 1) * a.J_pad + i]);
-                            nmax_next = __ldg(&a.nq[q + 1]) + a.n_aux;
-                        }
-                    } else {  // padding beyond the last pair
-                        sp = 0.0f;
-                        f = 0.5f;
-                        mg = 0.0f;
-                        g_next = 0x7FFFFFFF;
-                    }
-                }
-                float w[8];
-#pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    const float da = f + (mg - (float)e), db = f + (mg - (float)(e + 1));
-                    const float rr = sp * rcp_approx(da * db);
-                    w[e] = db * rr;
-                    w[e + 1] = da * rr;
-                }
-                mg -= 8.0f;
-                const uint32_t off = row + (((uint32_t)cc ^ sw) << 4);
-                if (kHalf) {
-                    st_shared_v4(a_hi(st) + off, pack_f16(w[0], w[1]), pack_f16(w[2], w[3]),
-                                 pack_f16(w[4], w[5]), pack_f16(w[6], w[7]));
-                } else {
-                    uint32_t h[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) h[e] = pack_bf16(w[2 * e], w[2 * e + 1]);
-                    st_shared_v4(a_hi(st) + off, h[0], h[1], h[2], h[3]);
-                    if (kSplit) {
-                        uint32_t lo[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float h0 = __uint_as_float(h[e] << 16);
-                            const float h1 = __uint_as_float(h[e] & 0xFFFF0000u);
-                            lo[e] = pack_bf16(w[2 * e] - h0, w[2 * e + 1] - h1);
-                        }
-                        st_shared_v4(a_lo(st) + off, lo[0], lo[1], lo[2], lo[3]);
-                    }
-                }
+            // up to 64 weights, fully unrolled per group count
+            const uint32_t a_row = a_hi(st) + row;
+            switch (ng) {
+                case 2: gen_groups<2, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                case 4: gen_groups<4, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                case 6: gen_groups<6, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                default: gen_groups<8, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
             }
             fence_proxy_async();
             mbar_arrive(full_bar(st));
+            cur = nxt;
         }
 
-        // ---------------- epilogue: TMEM -> maps + argmax keys ----------------
+        // ---------------- epilogue: TMEM -> smem tile -> maps + argmax keys ----------------
         mbar_wait(accum_bar, 0, abort_flag, a.status);
         tc_fence_after();
-        const bool valid = i < a.J;
+        fence_proxy_async();
+        // every MMA has completed (and with it every TMA load it consumed), so the
+        // stage buffers are free: candidate r's frames go to column r of mt
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         for (int j0 = 0; j0 < a.N; j0 += 16) {
             float v[16];
             tmem_ld16(trow + (uint32_t)j0, v);
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-                const int l = l0 + j0 + jj;
-                if (l < a.L) {
-                    if (a.maps != nullptr && valid) a.maps[(size_t)l * a.J + i] = v[jj];
-                    unsigned long long k = valid ? argmax_key(v[jj], (uint32_t)i) : 0ull;
-                    k = warp_max_u64(k);
-                    if (lane == 0) red[warp * a.N + j0 + jj] = k;
-                }
-            }
+            for (int jj = 0; jj < 16; ++jj) mt[(j0 + jj) * kMtStride + r] = v[jj];
         }
         tc_fence_before();
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        for (int j = threadIdx.x; j < a.N && l0 + j < a.L; j += 128) {
-            unsigned long long k = red[j];
+        const int64_t tile0 = (int64_t)blockIdx.x * 128;
+        const int n_rows = min(a.N, a.L - l0);
+        if (a.maps != nullptr) {  // warp w writes frame rows w, w + 4, ...
+            for (int fr = warp; fr < n_rows; fr += 4) {
+                float *dst = a.maps + (size_t)(l0 + fr) * a.J + tile0;
+                const float *srcr = mt + fr * kMtStride;
 #pragma unroll
-            for (int w2 = 1; w2 < 4; ++w2) {
-                const unsigned long long t = red[w2 * a.N + j];
-                k = t > k ? t : k;
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int k = 2 * (lane + 32 * hh);
+                    const float2 val = *reinterpret_cast<const float2 *>(srcr + k);
+                    if (a.vec_maps && tile0 + k + 1 < a.J) {
+                        *reinterpret_cast<float2 *>(dst + k) = val;
+                    } else {
+                        if (tile0 + k < a.J) dst[k] = val.x;
+                        if (tile0 + k + 1 < a.J) dst[k + 1] = val.y;
+                    }
+                }
             }
-            a.part[(size_t)(l0 + j) * a.n_tiles + blockIdx.x] = k;
+        }
+        // first maximiser per frame: threads 2f and 2f+1 scan even / odd candidates
+        for (int fr = r >> 1; fr < n_rows + 63 - ((n_rows + 63) % 64); fr += 64) {
+            const int h = r & 1;
+            unsigned long long key = 0ull;
+            if (fr < n_rows) {
+                uint32_t bo = 0u;
+                int bk = -1;
+                const float *row_p = mt + fr * kMtStride;
+                const int kmax = (int)min((int64_t)128, a.J - tile0);
+                for (int k = h; k < kmax; k += 2) {
+                    const uint32_t o = ordered_value(row_p[k]);
+                    if (bk < 0 || o > bo) {
+                        bo = o;
+                        bk = k;
+                    }
+                }
+                if (bk >= 0)
+                    key = ((unsigned long long)bo << 32) |
+                          (unsigned long long)(0xFFFFFFFFu - (uint32_t)(tile0 + bk));
+            }
+            const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, 1);
+            key = other > key ? other : key;
+            if (h == 0 && fr < n_rows) a.part[(size_t)(l0 + fr) * a.n_tiles + blockIdx.x] = key;
         }
     } else if (warp == kTmaWarp) {
         // ---------------- B loads (GCC samples) ----------------
@@ -434,8 +546,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant
                 tc_fence_after();
                 const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
                 const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
+                const int nk = __ldg(&a.ctab[c]).w;  // 16-lag steps holding lags of the pair
 #pragma unroll
                 for (int kk = 0; kk < kChunk / 16; ++kk) {
+                    if (kk >= nk) break;
                     const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
                     mma_f16(tmem, dah + adv, dbh + adv, a.idesc, (c | kk) != 0);
                     if (kSplit) {
@@ -512,7 +626,7 @@ cudaError_t encode_xi_map(void *xi16, int rows, int S_pad, int N, void *map_out)
 }
 
 cudaError_t launch_gcc_samples_tc(const float2 *psi, int L, int Q, int K, const int32_t *nq,
-                                  const int32_t *off8, int n_aux, const float2 *twid,
+                                  const int32_t *offc, int n_aux, const float2 *twid,
                                   uint16_t *xi16, int L_pad, int S_pad, int fmt, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * (size_t)(K + K / 2 + 1);
@@ -524,7 +638,7 @@ cudaError_t launch_gcc_samples_tc(const float2 *psi, int L, int Q, int K, const 
         if (e != cudaSuccess) return e;
         attr[fmt] = true;
     }
-    kern<<<dim3(Q, L), 128, smem, s>>>(psi, Q, K, nq, off8, n_aux, twid, xi16, L_pad, S_pad);
+    kern<<<dim3(Q, L), 128, smem, s>>>(psi, Q, K, nq, offc, n_aux, twid, xi16, L_pad, S_pad);
     return cudaGetLastError();
 }
 
@@ -533,16 +647,17 @@ int interp_tc_frames_per_cta(int L) {
     return n > 256 ? 256 : n;
 }
 
-cudaError_t launch_interp_tc(const void *xi_map, int N, const int32_t *x, int64_t J_pad,
-                             int64_t J, int Q, const int32_t *nq, int n_aux, int xf, int S_pad,
-                             int L_pad, int L, int precision, float *maps,
+cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const int4 *ctab,
+                             int64_t J_pad, int64_t J, int Q, const int32_t *nq, int n_aux,
+                             int xf, int S_pad, int L_pad, int L, int precision, float *maps,
                              unsigned long long *part, int n_tiles, int *status, cudaStream_t s) {
     // N is the plan's frames per CTA: the height of the tensor map's box.
     if (L == 0) return cudaSuccess;
     if (N < 16 || N > 256 || (N & 15)) return cudaErrorInvalidValue;
     const bool split = precision == SRP_PREC_FP32, half = precision == SRP_PREC_FP16;
     TcArgs a;
-    a.x = x;
+    a.xs = xs;
+    a.ctab = ctab;
     a.J_pad = J_pad;
     a.J = J;
     a.Q = Q;
@@ -561,17 +676,21 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int32_t *x, int64_
     while (cols < (uint32_t)N) cols <<= 1;
     a.tmem_cols = cols;
     const size_t stage = (split ? 2 : 1) * (size_t)(kATile + (uint32_t)N * 128u);
-    const size_t fixed = 1024 + 1024 + 4 * sizeof(unsigned long long) * (size_t)N;
-    // two stages (or more if they fit in half the SM) and at most four
+    const size_t fixed = 1024 + 1024 + (size_t)kXRing * 128 * sizeof(int2);
+    const size_t tile_bytes = (size_t)N * kMtStride * sizeof(float);  // epilogue tile
+    // two stages (or more if they fit in half the SM) and at most four; the
+    // stages must also hold the epilogue tile
     int stages = (int)((113 * 1024 - fixed) / stage);
     if (stages < 2) stages = (int)((227 * 1024 - fixed) / stage);
     if (stages > 4) stages = 4;
-    if (stages < 2) return cudaErrorInvalidConfiguration;
+    while (stages * stage < tile_bytes && fixed + (stages + 1) * stage <= 227 * 1024) ++stages;
+    if (stages < 2 || stages * stage < tile_bytes) return cudaErrorInvalidConfiguration;
     a.stages = stages;
     a.maps = maps;
     a.part = part;
     a.n_tiles = n_tiles;
     a.status = status;
+    a.vec_maps = (maps != nullptr && (J % 2) == 0 && (reinterpret_cast<uintptr_t>(maps) & 7) == 0);
     const size_t smem = fixed + stage * (size_t)stages;
     const int grid_y = (L + N - 1) / N;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(xi_map);

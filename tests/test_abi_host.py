@@ -92,16 +92,16 @@ def test_footprint_counts_every_buffer():
     fp = srp.srp_plan_footprint(d)
     assert fp == info.device_bytes
     Q, Jp, Lp = 28, 1024, 64
-    S8 = int(np.sum(-(-(2 * nq + 5) // 8) * 8))
-    S8p = -(-S8 // 64) * 64
+    Sc = int(np.sum(-(-(2 * nq + 5) // 64) * 64))  # each pair padded to 64-lag chunks
     common = 4 + 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
     # tensor-core engine: twiddles, 8-aligned pair offsets, split 16-bit GCC samples
-    assert fp == common + 8 * 1024 + 4 * Q + 2 * 2 * Lp * S8p
+    tc_tables = 4 * Q + 8 * Q * Jp + 16 * (Sc // 64)  # pair offsets, (TDOA, sp), chunk table
+    assert fp == common + 8 * 1024 + tc_tables + 2 * 2 * Lp * Sc
     d3, keep3 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, engine="cuda_cores")
     Sp = -(-info.S // 64) * 64
     assert srp.srp_plan_footprint(d3) == common + 8 * 1024 + 4 * Sp * Lp
     d4, keep4 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision="bf16")
-    assert srp.srp_plan_footprint(d4) == common + 8 * 1024 + 4 * Q + 2 * Lp * S8p
+    assert srp.srp_plan_footprint(d4) == common + 8 * 1024 + tc_tables + 2 * Lp * Sc
     d2, keep2 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional")
     fp2 = srp.srp_plan_footprint(d2)
     assert fp2 == 4 + 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
