@@ -144,6 +144,9 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         }
         lay.Sc = (int)sc;
         lay.n_chunks = (int)(sc / kLagPad);
+        // a chunk with two or more 16-lag steps feeds the second accumulator
+        for (int q = 0; q < lay.Q; ++q)
+            if (2 * (lay.Nq[q] + d->n_aux) + 1 > 16) lay.par1_used = 1;
         lay.N_tc = interp_tc_frames_per_cta(d->max_frames);
     }
 
@@ -343,8 +346,9 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     }
     record(h, 2, s);
     if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
-        SRP_CUDA(launch_interp_tc(h->xi_map, lay.N_tc, h->d_xs, h->d_ctab, lay.J_pad, lay.J,
-                                  lay.Q, h->d_nq, lay.n_aux, lay.xf, lay.Sc, lay.L_pad, L,
+        SRP_CUDA(launch_interp_tc(h->xi_map, lay.N_tc, h->d_xs, h->d_ctab, lay.par1_used,
+                                  lay.J_pad, lay.J, lay.Q, h->d_nq, lay.n_aux, lay.xf, lay.Sc,
+                                  lay.L_pad, L,
                                   h->precision, d_maps, h->d_part, lay.n_tiles, h->d_status, s),
                  "tensor-core interpolation kernel");
     } else if (h->mode == SRP_MODE_NYQUIST) {

@@ -28,7 +28,7 @@ struct Layout {
     int L_max = 0, L_pad = 0, n_tiles = 0;
     std::vector<int32_t> Nq, off, pm, pmp;  // per pair
     // tensor-core lag layout: pair q owns ceil(N'_q / 64) chunks of 64 slots
-    int Sc = 0, n_chunks = 0, N_tc = 0;
+    int Sc = 0, n_chunks = 0, N_tc = 0, par1_used = 0;
     bool tc = false;    // the Nyquist map runs on the tensor cores
     std::vector<int32_t> offc;
     // byte counts of every device buffer, in allocation order
@@ -101,9 +101,10 @@ cudaError_t launch_gcc_samples_tc(const float2 *psi, int L, int Q, int K, const 
                                   uint16_t *xi16, int L_pad, int S_pad, int fmt, cudaStream_t s);
 int interp_tc_frames_per_cta(int L);
 cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const int4 *ctab,
-                             int64_t J_pad, int64_t J, int Q, const int32_t *nq, int n_aux,
-                             int xf, int S_pad, int L_pad, int L, int precision, float *maps,
-                             unsigned long long *part, int n_tiles, int *status, cudaStream_t s);
+                             int par1_used, int64_t J_pad, int64_t J, int Q, const int32_t *nq,
+                             int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
+                             float *maps, unsigned long long *part, int n_tiles, int *status,
+                             cudaStream_t s);
 cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,
                           float *peak, cudaStream_t s);
 

@@ -39,8 +39,8 @@ namespace {
 
 using namespace dev;
 
-constexpr int kThreads = 192;        // warps 0-3: A generation + epilogue; 4: TMA; 5: MMA
-constexpr int kTmaWarp = 4, kMmaWarp = 5;
+constexpr int kThreads = 224;        // warps 0-3: A generation + epilogue; 4: TMA; 5, 6: MMA
+constexpr int kTmaWarp = 4, kMmaWarp0 = 5;
 constexpr int kChunk = 64;           // lags per pipeline stage
 constexpr uint32_t kATile = 128u * 128u;  // 128 candidates x 64 lags x 2 B
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
@@ -300,6 +300,7 @@ struct TcArgs {
     int n_tiles;
     int *status;
     int vec_maps;           // maps rows are 8-byte aligned (float2 stores)
+    int par1_used;          // some chunk has two or more 16-lag steps
 };
 
 // Weights of NG groups of 8 lags for one candidate row of the A tile(s):
@@ -344,7 +345,7 @@ __device__ __forceinline__ void gen_groups(uint32_t a_row, uint32_t sw, float f,
 }
 
 template <bool kSplit, bool kHalf>
-__global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
                                                            const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // control block, then 1024-aligned stages, then the argmax scratch
@@ -376,9 +377,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(full_bar(s), 128 + 1);
-            mbar_init(empty_bar(s), 1);
+            mbar_init(empty_bar(s), 2);
         }
-        mbar_init(accum_bar, 1);
+        mbar_init(accum_bar, 2);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -461,6 +462,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant
         for (int j0 = 0; j0 < a.N; j0 += 16) {
             float v[16];
             tmem_ld16(trow + (uint32_t)j0, v);
+            if (a.par1_used) {
+                float v1[16];
+                tmem_ld16(trow + (uint32_t)(a.N + j0), v1);
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) v[jj] += v1[jj];
+            }
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) mt[(j0 + jj) * kMtStride + r] = v[jj];
         }
@@ -537,8 +544,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant
             }
         }
     } else {
-        // ---------------- MMA issue ----------------
+        // ---------------- MMA issue: two warps, by 16-lag step parity ----------------
+        // One 128 x N x 16 MMA is small at N = 64, so the steps are spread over
+        // two accumulators (TMEM columns [0, N) and [N, 2N)), each fed by its
+        // own issuing warp; the epilogue adds them.
+        const int par = warp - kMmaWarp0;
         if (lane == 0) {
+            const uint32_t dt = tmem + (uint32_t)(par * a.N);
+            uint32_t acc = 0;  // the first MMA into the accumulator overwrites it
             for (int c = 0; c < a.n_chunks; ++c) {
                 const int st = c % a.stages;
                 const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
@@ -547,14 +560,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_interp_tc(const __grid_constant
                 const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
                 const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
                 const int nk = __ldg(&a.ctab[c]).w;  // 16-lag steps holding lags of the pair
-#pragma unroll
-                for (int kk = 0; kk < kChunk / 16; ++kk) {
-                    if (kk >= nk) break;
+                for (int kk = par; kk < nk; kk += 2) {
                     const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
-                    mma_f16(tmem, dah + adv, dbh + adv, a.idesc, (c | kk) != 0);
+                    mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
+                    acc = 1;
                     if (kSplit) {
-                        mma_f16(tmem, dah + adv, dbl + adv, a.idesc, 1);
-                        mma_f16(tmem, dal + adv, dbh + adv, a.idesc, 1);
+                        mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
+                        mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
                     }
                 }
                 mma_commit(empty_bar(st));
@@ -648,9 +660,10 @@ int interp_tc_frames_per_cta(int L) {
 }
 
 cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const int4 *ctab,
-                             int64_t J_pad, int64_t J, int Q, const int32_t *nq, int n_aux,
-                             int xf, int S_pad, int L_pad, int L, int precision, float *maps,
-                             unsigned long long *part, int n_tiles, int *status, cudaStream_t s) {
+                             int par1_used, int64_t J_pad, int64_t J, int Q, const int32_t *nq,
+                             int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
+                             float *maps, unsigned long long *part, int n_tiles, int *status,
+                             cudaStream_t s) {
     // N is the plan's frames per CTA: the height of the tensor map's box.
     if (L == 0) return cudaSuccess;
     if (N < 16 || N > 256 || (N & 15)) return cudaErrorInvalidValue;
@@ -673,7 +686,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     const uint32_t ab = half ? 0u : 1u;
     a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
     uint32_t cols = 32;
-    while (cols < (uint32_t)N) cols <<= 1;
+    while (cols < (uint32_t)(2 * N)) cols <<= 1;  // two accumulators
     a.tmem_cols = cols;
     const size_t stage = (split ? 2 : 1) * (size_t)(kATile + (uint32_t)N * 128u);
     const size_t fixed = 1024 + 1024 + (size_t)kXRing * 128 * sizeof(int2);
@@ -690,6 +703,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.part = part;
     a.n_tiles = n_tiles;
     a.status = status;
+    a.par1_used = par1_used;
     a.vec_maps = (maps != nullptr && (J % 2) == 0 && (reinterpret_cast<uintptr_t>(maps) & 7) == 0);
     const size_t smem = fixed + stage * (size_t)stages;
     const int grid_y = (L + N - 1) / N;
