@@ -35,6 +35,9 @@ METRIC = "SRP cells*pairs/s (Nyquist vs conventional) at stated map error; p50/p
 UNIT = "cells*pairs/s"
 WORKLOAD = dict(name="room_3d", M=8, J=480000, K=1024, L=64, n_aux=2, fs=16000.0, snr_db=10.0)
 FLUSH_BYTES = 256 << 20
+# DRAM read + write bytes of one k_interp_tc<split> launch on this workload,
+# from ncu (profiles/k_interp_tc_room_3d.md); None once the kernel changes.
+K3_TRAFFIC_BYTES = 183.1e6
 
 
 def config_dict(Q, S):
@@ -318,9 +321,11 @@ def bench_ours(args):
         "map_error_bound": "FP32 path: max |map - FP64 oracle| <= 1e-4 x peak (tests)",
         "stage_ms": {k: v for k, v in srp.srp_stage_times(plans["conventional"].handle).items()},
         "roofline": {
-            "kernel": "k_interp_tc<split> (sinc interpolation + pair sum, tcgen05, FP32 as 3 BF16 products)",
+            "kernel": "k_interp_tc<split> (on-chip sinc weights + tcgen05 MMA, FP32 as 3 BF16 products)",
             "bound": "tensor", "achieved": achieved, "peak": split_peak, "unit": "TFLOP/s",
-            "frac": achieved / split_peak, "traffic": None,
+            "frac": achieved / split_peak,
+            "traffic": K3_TRAFFIC_BYTES,
+            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
             "algorithmic": f"2*J*S*L = {flops:.4g} flop per launch (S={S} lags); "
                            f"{k3_ms:.4f} ms per launch",
             "peak_source": f"measured bf16 {bf16_peak:.1f} TFLOP/s ({peak_src}) / 3 products",
