@@ -120,7 +120,12 @@ typedef struct {
     int32_t max_nq;      /* max_q N_q */
     int32_t x_frac_bits; /* fractional bits of the fixed-point TDOA table */
     int32_t max_frames;
-    size_t device_bytes; /* bytes srp_plan allocates on the device */
+    int32_t tensor_cores; /* 1: the map runs on the tensor cores (tcgen05), 0: CUDA cores.
+                             SRP_ENGINE_AUTO keeps an FP32 plan on CUDA cores when its
+                             reduction is long enough for the tensor-core FP32
+                             accumulation bias (about 1.5e-8 per 16-element step) to
+                             reach half the 1e-4 tolerance */
+    size_t device_bytes;  /* bytes srp_plan allocates on the device */
 } srp_plan_info;
 
 typedef struct srp_plan_s *srp_handle;

@@ -23,6 +23,7 @@ constexpr int kMaxK = 8192;
 constexpr int kMaxFrames = 65536;
 constexpr int64_t kMaxJ = (int64_t)INT32_MAX - (1 << 20);
 constexpr int kMaxLagSpan = 8192;  // 2 (N_q + N_aux) + 1 per pair
+constexpr double kTcAccumBias = 1.5e-8;  // relative, per MMA step accumulated in TMEM
 
 srp_status fail(srp_status st, const std::string &msg) {
     g_err = msg;
@@ -60,6 +61,13 @@ struct DeviceGuard {
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 bool finite3(const double *p) { return isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]); }
+
+// Slots of pair q on the tensor-core reduction axis: its critical lags
+// 2(N_q + N_aux) + 1 (Nyquist) or its bins as (re, im) pairs, 2 Kb (conventional).
+int64_t tc_span(const srp_plan_desc *d, const Layout &lay, int q) {
+    if (d->mode == SRP_MODE_NYQUIST) return 2 * ((int64_t)lay.Nq[q] + d->n_aux) + 1;
+    return 2 * (int64_t)lay.Kb;
+}
 
 // Validate the descriptor and compute every size of the plan.  Host only.
 srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
@@ -130,23 +138,32 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     }
     lay.S = (int)S;
     lay.S_pad = (int)round_up(S, kLagPad);
-    // The Nyquist map runs on the tensor cores unless CUDA cores are asked
-    // for; the conventional map and the CUDA-core engine are FP32 only.
-    lay.tc = d->mode == SRP_MODE_NYQUIST && d->engine == SRP_ENGINE_AUTO;
+    // Both maps run on the tensor cores unless CUDA cores are asked for; the
+    // CUDA-core engine is FP32 only.  FP32 accumulation in TMEM carries a
+    // systematic relative bias of about kTcAccumBias per accumulated MMA step
+    // (measured on GB300), so an FP32 plan whose reduction is long enough for
+    // that bias to reach half of the 1e-4 tolerance (long conventional sums:
+    // many pairs x many bins) runs on the exact CUDA-core kernels instead.
+    lay.tc = d->engine == SRP_ENGINE_AUTO;
+    if (lay.tc && d->precision == SRP_PREC_FP32) {
+        int64_t steps = 0;  // 16-slot MMA steps per tile
+        for (int q = 0; q < lay.Q; ++q) steps += round_up(tc_span(d, lay, q), 16) / 16;
+        const double adds = 3.0 * (double)steps / 2.0;  // 3 products, 2 accumulators
+        if (adds * kTcAccumBias > 5e-5) lay.tc = false;
+    }
     if (!lay.tc && d->precision != SRP_PREC_FP32)
-        return fail(SRP_ERR_UNSUPPORTED,
-                    "BF16/FP16 need the Nyquist mode on the tensor-core engine");
+        return fail(SRP_ERR_UNSUPPORTED, "BF16/FP16 need the tensor-core engine");
     if (lay.tc) {
+        // reduction axis per pair: the critical lags (Nyquist) or the bins as
+        // (re, im) element pairs (conventional), padded to 64-slot chunks
         int64_t sc = 0;
         for (int q = 0; q < lay.Q; ++q) {
             lay.offc.push_back((int32_t)sc);
-            sc += round_up(2 * (int64_t)lay.Nq[q] + 2 * (int64_t)d->n_aux + 1, kLagPad);
+            sc += round_up(tc_span(d, lay, q), kLagPad);
+            if (tc_span(d, lay, q) > 16) lay.par1_used = 1;  // a chunk with 2+ MMA steps
         }
         lay.Sc = (int)sc;
         lay.n_chunks = (int)(sc / kLagPad);
-        // a chunk with two or more 16-lag steps feeds the second accumulator
-        for (int q = 0; q < lay.Q; ++q)
-            if (2 * (lay.Nq[q] + d->n_aux) + 1 > 16) lay.par1_used = 1;
         lay.N_tc = interp_tc_frames_per_cta(d->max_frames);
     }
 
@@ -207,6 +224,7 @@ void fill_info(const Layout &lay, srp_plan_info *info) {
     info->max_nq = lay.max_nq;
     info->x_frac_bits = lay.xf;
     info->max_frames = lay.L_max;
+    info->tensor_cores = lay.tc ? 1 : 0;
     info->device_bytes = lay.total();
 }
 
@@ -288,17 +306,24 @@ srp_status build_tdoa(const srp_plan_desc *d, srp_plan_s *h) {
     }
     SRP_CUDA(cudaMemcpy(h->d_xs, xs.data(), lay.b_xs, cudaMemcpyHostToDevice),
              "upload tensor-core TDOA table");
-    // per chunk of 64 lag slots: pair, nmax_q - first slot (float bits), groups
-    // of 8 slots to generate (even) and 16-slot MMA steps holding lags
+    // per chunk of 64 slots: pair; nmax_q - first slot as float bits (Nyquist)
+    // or the chunk's first bin (conventional); 8-slot groups to generate
+    // (even); 16-slot MMA steps holding data
     std::vector<int4> ctab(lay.n_chunks);
+    const bool nyq = d->mode == SRP_MODE_NYQUIST;
     for (int q = 0; q < lay.Q; ++q) {
-        const int nmax = lay.Nq[q] + lay.n_aux, span = 2 * nmax + 1;
+        const int nmax = lay.Nq[q] + lay.n_aux;
+        const int span = nyq ? 2 * nmax + 1 : 2 * lay.Kb;
         for (int c0 = 0; c0 < span; c0 += kLagPad) {
-            const float moff = (float)(nmax - c0);
-            int32_t mbits;
-            memcpy(&mbits, &moff, sizeof mbits);
+            int32_t y;
+            if (nyq) {
+                const float moff = (float)(nmax - c0);
+                memcpy(&y, &moff, sizeof y);
+            } else {
+                y = c0 / 2;  // first bin: two slots per bin
+            }
             const int nk = (std::min(kLagPad, span - c0) + 15) / 16;
-            ctab[(lay.offc[q] + c0) / kLagPad] = make_int4(q, mbits, 2 * nk, nk);
+            ctab[(lay.offc[q] + c0) / kLagPad] = make_int4(q, y, 2 * nk, nk);
         }
     }
     SRP_CUDA(cudaMemcpy(h->d_ctab, ctab.data(), lay.b_ctab, cudaMemcpyHostToDevice),
@@ -331,8 +356,13 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
         ++launches;
     }
     record(h, 1, s);
-    if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
-        const int fmt = h->precision == SRP_PREC_FP32 ? 1 : (h->precision == SRP_PREC_FP16 ? 2 : 0);
+    const int fmt = h->precision == SRP_PREC_FP32 ? 1 : (h->precision == SRP_PREC_FP16 ? 2 : 0);
+    if (h->mode == SRP_MODE_CONV && lay.tc) {
+        SRP_CUDA(launch_conv_operand_tc(psi, L, lay.Q, lay.K, h->d_offc, h->d_xi16, lay.L_pad,
+                                        lay.Sc, fmt, s), "conventional operand kernel");
+        h->stage_ran[kStageGcc] = 1;
+        ++launches;
+    } else if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
         SRP_CUDA(launch_gcc_samples_tc(psi, L, lay.Q, lay.K, h->d_nq, h->d_offc, lay.n_aux,
                                        h->d_twid, h->d_xi16, lay.L_pad, lay.Sc, fmt, s),
                  "GCC sample kernel");
@@ -345,12 +375,12 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
         ++launches;
     }
     record(h, 2, s);
-    if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
+    if (lay.tc) {
         SRP_CUDA(launch_interp_tc(h->xi_map, lay.N_tc, h->d_xs, h->d_ctab, lay.par1_used,
                                   lay.J_pad, lay.J, lay.Q, h->d_nq, lay.n_aux, lay.xf, lay.Sc,
-                                  lay.L_pad, L,
-                                  h->precision, d_maps, h->d_part, lay.n_tiles, h->d_status, s),
-                 "tensor-core interpolation kernel");
+                                  lay.L_pad, L, h->precision, h->mode == SRP_MODE_CONV ? 1 : 0,
+                                  lay.K, d_maps, h->d_part, lay.n_tiles, h->d_status, s),
+                 "tensor-core map kernel");
     } else if (h->mode == SRP_MODE_NYQUIST) {
         SRP_CUDA(launch_interp_simt(h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq, h->d_off, lay.n_aux,
                                     lay.xf, h->d_xi, lay.L_pad, L, d_maps, h->d_part, lay.n_tiles,

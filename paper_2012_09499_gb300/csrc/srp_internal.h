@@ -103,8 +103,10 @@ int interp_tc_frames_per_cta(int L);
 cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const int4 *ctab,
                              int par1_used, int64_t J_pad, int64_t J, int Q, const int32_t *nq,
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
-                             float *maps, unsigned long long *part, int n_tiles, int *status,
-                             cudaStream_t s);
+                             int conv, int K, float *maps, unsigned long long *part, int n_tiles,
+                             int *status, cudaStream_t s);
+cudaError_t launch_conv_operand_tc(const float2 *psi, int L, int Q, int K, const int32_t *offc,
+                                   uint16_t *b16, int L_pad, int S_pad, int fmt, cudaStream_t s);
 cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,
                           float *peak, cudaStream_t s);
 

@@ -1,6 +1,8 @@
-// Tensor-core (tcgen05 / TMEM / TMA) kernels of the Nyquist SRP path:
+// Tensor-core (tcgen05 / TMEM / TMA) kernels of the SRP map:
 //   k_gcc_samples_tc  critical GCC samples (Eq. GCC_IFT at tau = nT) as 16-bit
 //                     operands, sign-folded and split for the FP32 path
+//   k_conv_operand_tc (a_k/K)(Re psi, Im psi) as 16-bit operands for the
+//                     conventional map (Eq. GCC_IFT at every TDOA, Sec. 2.4)
 //   k_interp_tc       map[l][i] = sum_q sum_n xi_q(n) sinc(x_iq - n)
 //                     (Eq. SRPapprox summed over pairs, Eq. SRP_T_IFT) as one
 //                     (J x S) x (S x L) contraction with the pair sum as the
@@ -22,6 +24,12 @@
 // 16-lag MMA steps to issue (trailing empty steps are skipped).  The plan also
 // holds, per (pair, candidate), the fixed-point TDOA and sp = (-1)^x0
 // sin(pi f)/pi computed in FP64, so no sine is evaluated here.
+//
+// The same kernel (kConv) computes the conventional map as the contraction of
+// the steering matrix [cos theta, -sin theta], theta = 2 pi k x_iq / K, with
+// (a_k/K)(Re psi, Im psi) over (pair, bin, re/im): each thread seeds
+// e^{-j theta} exactly every 32 bins (phase ((k x0 mod K) + k f)/K) and
+// rotates by e^{-j 2 pi x / K} in between.
 //
 // FP32 precision uses three BF16 products per step (A_hi B_hi + A_hi B_lo +
 // A_lo B_hi, hi = bf16(v), lo = bf16(v - hi)); BF16 and FP16 precision use one.
@@ -281,11 +289,41 @@ __global__ void __launch_bounds__(128) k_gcc_samples_tc(
 }
 
 // ---------------------------------------------------------------------------
+// Conventional operand B: slot offc[q] + 2k (+1) of row l holds
+// (a_k/K) Re psi_q(k) (and (a_k/K) Im psi_q(k)), as bf16 (hi, lo) or fp16.
+// ---------------------------------------------------------------------------
+template <int kFmt>  // 0: bf16, 1: bf16 hi/lo split, 2: fp16
+__global__ void __launch_bounds__(128) k_conv_operand_tc(const float2 *__restrict__ psi, int Q,
+                                                         int K, const int32_t *__restrict__ offc,
+                                                         uint16_t *__restrict__ b16, int L_pad,
+                                                         int S_pad) {
+    const int Kb = K / 2 + 1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y, l = blockIdx.z;
+    if (k >= Kb) return;
+    const float2 v = psi[((size_t)l * Q + q) * Kb + k];
+    const float ak = ((k == 0 || 2 * k == K) ? 1.0f : 2.0f) / (float)K;
+    const float re = ak * v.x, im = ak * v.y;
+    const size_t hi = (size_t)l * S_pad + offc[q] + 2 * k;
+    uint32_t h, lo = 0;
+    if (kFmt == 2) {
+        h = pack_f16(re, im);
+    } else {
+        h = pack_bf16(re, im);
+        if (kFmt == 1)
+            lo = pack_bf16(re - __uint_as_float(h << 16), im - __uint_as_float(h & 0xFFFF0000u));
+    }
+    *reinterpret_cast<uint32_t *>(b16 + hi) = h;
+    if (kFmt == 1) *reinterpret_cast<uint32_t *>(b16 + hi + (size_t)L_pad * S_pad) = lo;
+}
+
+// ---------------------------------------------------------------------------
 // The contraction.
 // ---------------------------------------------------------------------------
 struct TcArgs {
     const int2 *xs;         // [Q][J_pad] (fixed-point TDOA, bits of sp)
-    const int4 *ctab;       // [n_chunks] (pair, bits of nmax_q - first lag slot, groups, MMA steps)
+    int K;                  // DFT length (conventional map)
+    const int4 *ctab;       // [n_chunks] (pair, nmax_q - first lag slot as float bits or, for
+                            // the conventional map, first bin; groups; MMA steps)
     int64_t J_pad, J;
     int Q;
     const int32_t *nq;      // [Q]
@@ -344,7 +382,44 @@ __device__ __forceinline__ void gen_groups(uint32_t a_row, uint32_t sw, float f,
     }
 }
 
-template <bool kSplit, bool kHalf>
+// Steering weights of NG groups (4 bins each) for this thread's row: the
+// element pair (cos theta_k, -sin theta_k) of bins k0, k0 + 1, ..., i.e.
+// z = e^{-j theta_k}, starting from z0 and multiplied per bin by
+// w' = (p, q) = e^{-j 2 pi x / K}: z w' = (a p - b q, b p + a q) for z = (a, b).
+template <int NG, bool kSplit, bool kHalf>
+__device__ __forceinline__ void gen_steer(uint32_t a_row, uint32_t sw, float za, float zb,
+                                          float p, float q) {
+    uint64_t z = pk2(za, zb);
+    const uint64_t pp = pk2(p, p), qq = pk2(-q, q);
+#pragma unroll
+    for (int cc = 0; cc < NG; ++cc) {
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 v = upk2(z);
+            const uint64_t t = mul2(z, pp);
+            uint64_t zn;
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(zn) : "l"(pk2(v.y, v.x)), "l"(qq), "l"(t));
+            z = zn;
+            if (kHalf) {
+                hv[e] = pack_f16(v.x, v.y);
+            } else {
+                hv[e] = pack_bf16(v.x, v.y);
+                if (kSplit) {
+                    const uint64_t h2 = pk2(__uint_as_float(hv[e] << 16),
+                                            __uint_as_float(hv[e] & 0xFFFF0000u));
+                    const float2 lo = upk2(sub2(pk2(v.x, v.y), h2));
+                    lv[e] = pack_bf16(lo.x, lo.y);
+                }
+            }
+        }
+        const uint32_t off = a_row + (((uint32_t)cc ^ sw) << 4);
+        st_shared_v4(off, hv[0], hv[1], hv[2], hv[3]);
+        if (kSplit) st_shared_v4(off + kATile, lv[0], lv[1], lv[2], lv[3]);
+    }
+}
+
+template <bool kSplit, bool kHalf, bool kConv>
 __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
                                                            const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -399,6 +474,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
         // is never 0 unless f is.
         int q = -1;
         float sp = 0.0f, f = 0.5f, x0f = 0.0f;
+        int x0m = 0;              // conventional: x0 mod K
+        float wp = 1.0f, wq = 0.0f;  // conventional: e^{-j 2 pi x / K}
+        const float two_k = 2.0f / (float)a.K;
         // (TDOA, sp) of the first kXAhead pairs start streaming in now; pair p
         // sits in slot p % kXRing.  Pair q + 1 is read from its slot when pair q
         // starts, one chunk or more ahead of its use, and that read issues the
@@ -431,21 +509,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                 q = cur.x;
                 int x0;
                 decode_tdoa(nX, a.xf, x0, f);
-                if (f == 0.0f) f = 9.094947017729282e-13f;  // 2^-40, as in the plan
-                sp = __int_as_float(nsp);
-                x0f = (float)x0;
+                if (kConv) {
+                    x0m = ((x0 % a.K) + a.K) % a.K;
+                    float sn, cs;
+                    sincospif(((float)x0 + f) * two_k, &sn, &cs);
+                    wp = cs;
+                    wq = -sn;
+                } else {
+                    if (f == 0.0f) f = 9.094947017729282e-13f;  // 2^-40, as in the plan
+                    sp = __int_as_float(nsp);
+                    x0f = (float)x0;
+                }
                 if (q + 1 < a.Q) read_ring(q + 1);
             }
-            const float mc = x0f + __int_as_float(cur.y);  // x0 + nmax - first lag slot
+            const float mc = x0f + __int_as_float(cur.y);  // Nyquist: x0 + nmax - first lag slot
             const int ng = cur.z;
             if (c >= a.stages) mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status);
             // up to 64 weights, fully unrolled per group count
             const uint32_t a_row = a_hi(st) + row;
-            switch (ng) {
-                case 2: gen_groups<2, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                case 4: gen_groups<4, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                case 6: gen_groups<6, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                default: gen_groups<8, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+            if (kConv) {
+                // exact seed e^{-j theta_k0} for the chunk's first bin k0 = cur.y
+                const int k0 = cur.y;
+                const int rk = (int)(((long long)k0 * x0m) % a.K);
+                float sn, cs;
+                sincospif(fmaf((float)rk, two_k, (float)k0 * f * two_k), &sn, &cs);
+                switch (ng) {
+                    case 2: gen_steer<2, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
+                    case 4: gen_steer<4, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
+                    case 6: gen_steer<6, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
+                    default: gen_steer<8, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
+                }
+            } else {
+                switch (ng) {
+                    case 2: gen_groups<2, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                    case 4: gen_groups<4, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                    case 6: gen_groups<6, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                    default: gen_groups<8, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                }
             }
             fence_proxy_async();
             mbar_arrive(full_bar(st));
@@ -606,18 +706,18 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-template <bool kSplit, bool kHalf>
+template <bool kSplit, bool kHalf, bool kConv>
 cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_t smem,
                       cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf>,
+        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_interp_tc<kSplit, kHalf><<<dim3((unsigned)a.n_tiles, grid_y), kThreads, smem, s>>>(map, a);
+    k_interp_tc<kSplit, kHalf, kConv><<<dim3((unsigned)a.n_tiles, grid_y), kThreads, smem, s>>>(map, a);
     return cudaGetLastError();
 }
 
@@ -654,6 +754,17 @@ cudaError_t launch_gcc_samples_tc(const float2 *psi, int L, int Q, int K, const 
     return cudaGetLastError();
 }
 
+cudaError_t launch_conv_operand_tc(const float2 *psi, int L, int Q, int K, const int32_t *offc,
+                                   uint16_t *b16, int L_pad, int S_pad, int fmt, cudaStream_t s) {
+    if (L == 0) return cudaSuccess;
+    const int Kb = K / 2 + 1;
+    dim3 grid((Kb + 127) / 128, Q, L);
+    if (fmt == 0) k_conv_operand_tc<0><<<grid, 128, 0, s>>>(psi, Q, K, offc, b16, L_pad, S_pad);
+    else if (fmt == 1) k_conv_operand_tc<1><<<grid, 128, 0, s>>>(psi, Q, K, offc, b16, L_pad, S_pad);
+    else k_conv_operand_tc<2><<<grid, 128, 0, s>>>(psi, Q, K, offc, b16, L_pad, S_pad);
+    return cudaGetLastError();
+}
+
 int interp_tc_frames_per_cta(int L) {
     const int n = ((L + 15) / 16) * 16;
     return n > 256 ? 256 : n;
@@ -662,8 +773,8 @@ int interp_tc_frames_per_cta(int L) {
 cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const int4 *ctab,
                              int par1_used, int64_t J_pad, int64_t J, int Q, const int32_t *nq,
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
-                             float *maps, unsigned long long *part, int n_tiles, int *status,
-                             cudaStream_t s) {
+                             int conv, int K, float *maps, unsigned long long *part, int n_tiles,
+                             int *status, cudaStream_t s) {
     // N is the plan's frames per CTA: the height of the tensor map's box.
     if (L == 0) return cudaSuccess;
     if (N < 16 || N > 256 || (N & 15)) return cudaErrorInvalidValue;
@@ -704,13 +815,19 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.n_tiles = n_tiles;
     a.status = status;
     a.par1_used = par1_used;
+    a.K = K;
     a.vec_maps = (maps != nullptr && (J % 2) == 0 && (reinterpret_cast<uintptr_t>(maps) & 7) == 0);
     const size_t smem = fixed + stage * (size_t)stages;
     const int grid_y = (L + N - 1) / N;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(xi_map);
-    if (split) return launch_tc<true, false>(map, a, grid_y, smem, s);
-    if (half) return launch_tc<false, true>(map, a, grid_y, smem, s);
-    return launch_tc<false, false>(map, a, grid_y, smem, s);
+    if (conv) {
+        if (split) return launch_tc<true, false, true>(map, a, grid_y, smem, s);
+        if (half) return launch_tc<false, true, true>(map, a, grid_y, smem, s);
+        return launch_tc<false, false, true>(map, a, grid_y, smem, s);
+    }
+    if (split) return launch_tc<true, false, false>(map, a, grid_y, smem, s);
+    if (half) return launch_tc<false, true, false>(map, a, grid_y, smem, s);
+    return launch_tc<false, false, false>(map, a, grid_y, smem, s);
 }
 
 }  // namespace srp

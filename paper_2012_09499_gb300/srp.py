@@ -47,7 +47,8 @@ class srp_plan_info(ctypes.Structure):
         ("M", ctypes.c_int32), ("Q", ctypes.c_int32), ("K", ctypes.c_int32),
         ("Kb", ctypes.c_int32), ("J", ctypes.c_int64), ("n_aux", ctypes.c_int32),
         ("S", ctypes.c_int32), ("max_nq", ctypes.c_int32), ("x_frac_bits", ctypes.c_int32),
-        ("max_frames", ctypes.c_int32), ("device_bytes", ctypes.c_size_t),
+        ("max_frames", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
+        ("device_bytes", ctypes.c_size_t),
     ]
 
 

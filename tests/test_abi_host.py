@@ -102,9 +102,15 @@ def test_footprint_counts_every_buffer():
     assert srp.srp_plan_footprint(d3) == common + 8 * 1024 + 4 * Sp * Lp
     d4, keep4 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision="bf16")
     assert srp.srp_plan_footprint(d4) == common + 8 * 1024 + tc_tables + 2 * Lp * Sc
-    d2, keep2 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional")
-    fp2 = srp.srp_plan_footprint(d2)
-    assert fp2 == 4 + 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
+    base = 4 + 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
+    d2, keep2 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional",
+                      engine="cuda_cores")
+    assert srp.srp_plan_footprint(d2) == base
+    # conventional on the tensor cores: 2 Kb = 1026 slots per pair, padded to 1088
+    Scc = Q * 1088
+    d5, keep5 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional")
+    assert srp.srp_plan_footprint(d5) == (base + 4 * Q + 8 * Q * Jp + 16 * (Scc // 64)
+                                          + 2 * 2 * Lp * Scc)
 
 
 @pytest.mark.parametrize("field,value", [
@@ -120,9 +126,9 @@ def test_invalid_descriptors_rejected(field, value):
     assert e.value.status == srp.SRP_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("kw", [dict(mode="conventional", precision="bf16"),
+@pytest.mark.parametrize("kw", [dict(mode="conventional", precision="bf16", engine="cuda_cores"),
                                 dict(engine="cuda_cores", precision="fp16")])
-def test_half_precision_needs_tensor_core_nyquist(kw):
+def test_half_precision_needs_tensor_cores(kw):
     d, keep = _desc(**kw)
     with pytest.raises(srp.SrpError) as e:
         srp.srp_plan_describe(d)
@@ -142,3 +148,21 @@ def test_null_handle_rejected():
     with pytest.raises(srp.SrpError) as e:
         srp.srp_map(None, 1, 1, None, 1, stream=0)
     assert e.value.status == srp.SRP_ERR_INVALID_ARG
+
+
+def test_engine_choice_by_accumulation_bias():
+    """FP32 conventional plans with a long reduction stay on CUDA cores; the
+    benchmark's 3D workload and every Nyquist plan use the tensor cores."""
+    rng = np.random.default_rng(5)
+    mic8 = rng.uniform(-0.25, 0.25, (8, 3))
+    mic16 = rng.uniform(-0.5, 0.5, (16, 3))
+    grid = rng.uniform(0, 5, (100, 3))
+    cases = [(mic8, 1024, "conventional", "fp32", 1), (mic16, 2048, "conventional", "fp32", 0),
+             (mic16, 2048, "conventional", "bf16", 1), (mic16, 2048, "nyquist", "fp32", 1),
+             (mic8, 1024, "nyquist", "fp32", 1)]
+    for mic, K, mode, prec, tc in cases:
+        d, keep = srp.make_desc(mic, grid, 16000.0, 343.0, K, mode=mode, precision=prec)
+        info, _ = srp.srp_plan_describe(d)
+        assert info.tensor_cores == tc, (mic.shape[0], K, mode, prec)
+    d, keep = srp.make_desc(mic8, grid, 16000.0, 343.0, 1024, engine="cuda_cores")
+    assert srp.srp_plan_describe(d)[0].tensor_cores == 0

@@ -116,7 +116,8 @@ def test_plan_tdoa_matches_oracle(far):
 
 @pytest.mark.parametrize("mode,n_aux,engine", [
     ("nyquist", 2, "auto"), ("nyquist", 0, "auto"), ("nyquist", 2, "cuda_cores"),
-    ("nyquist", 0, "cuda_cores"), ("conventional", 0, "auto")])
+    ("nyquist", 0, "cuda_cores"), ("conventional", 0, "auto"),
+    ("conventional", 0, "cuda_cores")])
 def test_map_tiny_2d(mode, n_aux, engine):
     """2D square array, 41 x 41 grid, K = 512, L = 16 (several tiles, ragged tail)."""
     for seed in (0, 1):
@@ -156,7 +157,8 @@ def test_map_cross_spectra_input(mode):
 
 @pytest.mark.parametrize("mode,engine,precision", [
     ("nyquist", "auto", "fp32"), ("nyquist", "cuda_cores", "fp32"),
-    ("nyquist", "auto", "bf16"), ("nyquist", "auto", "fp16"), ("conventional", "auto", "fp32")])
+    ("nyquist", "auto", "bf16"), ("nyquist", "auto", "fp16"), ("conventional", "auto", "fp32"),
+    ("conventional", "cuda_cores", "fp32"), ("conventional", "auto", "bf16")])
 def test_map_room_3d_full_size_sampled(mode, engine, precision):
     """The 3D workload at full size (M = 8, J = 480000, K = 1024, L = 64) in
     the launch configuration the benchmark times; the oracle checks sampled
@@ -208,7 +210,7 @@ def test_map_room_3d_full_frame_nyquist():
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("mode,engine", [("nyquist", "auto"), ("nyquist", "cuda_cores"),
-                                         ("conventional", "auto")])
+                                         ("conventional", "auto"), ("conventional", "cuda_cores")])
 @pytest.mark.parametrize("J,L,max_frames", [(1, 1, 1), (129, 3, 5), (300, 37, 40), (257, 17, 17),
                                             (140, 300, 300), (131, 20, 270)])
 def test_ragged_sizes(mode, engine, J, L, max_frames):
@@ -309,8 +311,9 @@ def _cell_distance(grid, a, b):
     return np.linalg.norm(grid[a] - grid[b], axis=-1)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16"])
-def test_precision_two_sources(precision):
+@pytest.mark.parametrize("mode,precision", [("nyquist", "bf16"), ("nyquist", "fp16"),
+                                            ("conventional", "bf16")])
+def test_precision_two_sources(mode, precision):
     """2D array, grid 41 x 41, a second source at -6 dB, 160 frames:
     max |map - oracle| <= 1e-2 x peak; argmax within one grid cell of the
     oracle's on >= 99 % of the frames that are not documented ties, and every
@@ -322,9 +325,9 @@ def test_precision_two_sources(precision):
     for seed in range(10):
         cfg = synth.tiny_2d(seed=seed, L=16, second_source_db=-6.0)
         maps, idx, peak = gpu_run(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"],
-                                  cfg["Y"], "nyquist", 2, precision=precision)
+                                  cfg["Y"], mode, 2, precision=precision)
         check_self_consistent(maps, idx, peak)
-        ref = oracle_maps(cfg, "nyquist", 2)
+        ref = oracle_maps(cfg, mode, 2)
         pk = np.abs(ref).max(axis=1)
         worst = max(worst, float((np.abs(maps - ref).max(axis=1) / pk).max()))
         ridx = np.argmax(ref, axis=1)
@@ -338,3 +341,20 @@ def test_precision_two_sources(precision):
     assert worst <= TOL_HALF, worst
     # the statistic over frames that are not documented ties
     assert near >= 0.99 * (total - ties), (near, total, ties)
+
+
+def test_long_conventional_reduction_fp32():
+    """M = 16 (120 pairs), K = 2048: the FP32 conventional plan takes the exact
+    CUDA-core kernel (its tensor-core accumulation bias would exceed half the
+    tolerance) and meets 1e-4 x peak; BF16 stays on the tensor cores."""
+    rng = np.random.default_rng(21)
+    mic = rng.uniform(-0.5, 0.5, (16, 3)) + np.array([2.5, 2.0, 1.5])
+    grid = synth.box_grid((10, 8, 6), 0.5)
+    Y = synth.free_field_stft(rng, mic, [np.array([1.0, 3.0, 2.0])], 16000.0, 2048, 3, 10.0)
+    cfg = dict(mic=mic, grid=grid, fs=16000.0, c=343.0, K=2048, Y=Y)
+    ref = oracle_maps(cfg, "conventional", 0)
+    for prec, tol in [("fp32", TOL_FP32), ("bf16", TOL_HALF)]:
+        maps, idx, peak = gpu_run(mic, grid, 16000.0, 343.0, 2048, Y, "conventional", 0,
+                                  precision=prec)
+        check_self_consistent(maps, idx, peak)
+        check_against_oracle(maps, idx, ref, tol)
