@@ -226,6 +226,87 @@ SRP_API srp_status srp_last_launch_count(srp_handle h, int32_t *n);
 /* Release every device and host resource of the plan.  NULL is a no-op.  */
 SRP_API srp_status srp_destroy(srp_handle h);
 
+/* ------------------------------------------------------------------------
+ * Batched uneven instances.  The paper maps one array at a time; a batch
+ * maps several plans (arrays with their own M, J, K and geometry) in one
+ * CUDA-graph launch of three kernels: the PHAT cross spectra and contraction
+ * operands of every (plan, frame, pair) row; one persistent tensor-core
+ * kernel running the map contraction of every plan (Eq. SRPapprox, or
+ * Eq. GCC_IFT at every TDOA for the conventional map, summed over pairs) over
+ * a work list of (plan, 128-candidate tile, frame tile) items, spread over
+ * the SMs longest-first onto the least-loaded CTA; and the per-frame argmax
+ * of every plan.  Each plan's maps, argmax and peak are exactly what srp_map
+ * defines, up to floating-point rounding.
+ *
+ * The batch reads the plans' device tables in place (the plans must outlive
+ * the batch and must not be destroyed while it is in use) and owns its own
+ * operand buffer, argmax partials, work list and graph, so the plans stay
+ * usable by srp_map.  All plans must be on one device, share mode and
+ * precision, and run on the tensor cores (srp_plan_info.tensor_cores == 1);
+ * otherwise srp_batch_create returns SRP_ERR_UNSUPPORTED.  Calls on one batch
+ * share its buffers and must be ordered, like calls on one plan.
+ * ------------------------------------------------------------------------ */
+typedef struct srp_batch_s *srp_batch;
+
+/* Tile shape of the persistent contraction kernel. */
+typedef struct {
+    int32_t frames_per_tile; /* frames per work item (the MMA N): a multiple of 16 in
+                                [16, 128]; 0 = the largest max_frames rounded up to 16,
+                                at most 64 */
+    int32_t stages;          /* operand pipeline depth in [2, 4]; 0 = the most that fit */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM, 1 or 2; 0 = 2 where they fit */
+} srp_batch_tiles;
+
+typedef struct {
+    int32_t n;              /* plans in the batch */
+    int32_t items;          /* work items (every plan at max_frames) */
+    int32_t ctas;           /* persistent CTAs of the contraction kernel */
+    srp_batch_tiles tiles;  /* tile shape in use */
+    int32_t launches;       /* kernels per srp_map_batch call (all in one graph launch) */
+    int32_t tuned;          /* 1 once srp_batch_tune has chosen the tiles */
+    float tuned_ms;         /* one call with the chosen tiles, as timed by the tuner */
+    size_t device_bytes;    /* device bytes the batch owns (the plans' own excluded) */
+} srp_batch_info;
+
+/* Build a batch over n >= 1 plans (host array of handles, copied).  tiles
+ * may be NULL (defaults) and its zero fields take defaults.  Blocking.    */
+SRP_API srp_status srp_batch_create(const srp_handle *plans, int32_t n,
+                                    const srp_batch_tiles *tiles, srp_batch *out);
+
+/* Map every plan of the batch, as srp_map would each one.  All arguments are
+ * host arrays of n entries holding device pointers (or, for L, frame
+ * counts): d_in[i] input of plan i in its input_kind layout; L[i] in
+ * [0, max_frames of plan i] (a plan with L[i] = 0 is skipped and its
+ * pointers are not read); d_maps[i] device [L][J] maps of plan i or NULL
+ * (d_maps itself may be NULL: no maps); d_argmax[i] device [L] int32;
+ * d_peak[i] device [L] float or NULL (d_peak may be NULL).  Enqueues one
+ * host-to-device copy of the call table and one graph launch on s; waits
+ * only for the previous call's table copy to finish.                      */
+SRP_API srp_status srp_map_batch(srp_batch b, const void *const *d_in, const int32_t *L,
+                                 float *const *d_maps, int32_t *const *d_argmax,
+                                 float *const *d_peak, srp_stream_t s);
+
+/* Autotuner: runs the call above with every tile shape that fits (frames per
+ * item 16, 32, 64, 128 up to the largest L[i]; 2-4 stages; 1 or 2 CTAs per
+ * SM), times each by CUDA events on s, keeps the fastest and leaves the
+ * outputs of a final run with it.  Blocking.                              */
+SRP_API srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const int32_t *L,
+                                  float *const *d_maps, int32_t *const *d_argmax,
+                                  float *const *d_peak, srp_stream_t s);
+
+SRP_API srp_status srp_batch_get_info(srp_batch b, srp_batch_info *info);
+
+/* Milliseconds of the last call's three kernels in ms[0..n): 0 operands
+ * (cross spectra and GCC samples or bin operands), 1 map contraction,
+ * 2 argmax.  Waits for the last call to finish.                           */
+SRP_API srp_status srp_batch_stage_times(srp_batch b, float *ms, int32_t n);
+
+/* As srp_poll_device_status, for the batch's kernels.                      */
+SRP_API srp_status srp_batch_poll_device_status(srp_batch b, srp_stream_t s);
+
+/* Release the batch (not its plans).  NULL is a no-op.                    */
+SRP_API srp_status srp_batch_destroy(srp_batch b);
+
 /* Static description of a status code.                                    */
 SRP_API const char *srp_status_string(srp_status s);
 

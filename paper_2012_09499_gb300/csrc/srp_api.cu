@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "srp_internal.h"
@@ -24,39 +25,6 @@ constexpr int kMaxFrames = 65536;
 constexpr int64_t kMaxJ = (int64_t)INT32_MAX - (1 << 20);
 constexpr int kMaxLagSpan = 8192;  // 2 (N_q + N_aux) + 1 per pair
 constexpr double kTcAccumBias = 1.5e-8;  // relative, per MMA step accumulated in TMEM
-
-srp_status fail(srp_status st, const std::string &msg) {
-    g_err = msg;
-    return st;
-}
-
-srp_status cuda_fail(cudaError_t e, const char *what) {
-    g_err = std::string(what) + ": " + cudaGetErrorString(e);
-    return e == cudaErrorMemoryAllocation ? SRP_ERR_OOM : SRP_ERR_CUDA;
-}
-
-#define SRP_CUDA(call, what)                                   \
-    do {                                                       \
-        cudaError_t e_ = (call);                               \
-        if (e_ != cudaSuccess) return cuda_fail(e_, (what));   \
-    } while (0)
-
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) {
-            ok = false;
-            return;
-        }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
@@ -180,7 +148,7 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     lay.b_pairs = sizeof(int2) * lay.Q;
     lay.b_nq = sizeof(int32_t) * lay.Q;
     lay.b_off = sizeof(int32_t) * lay.Q;
-    lay.b_x = sizeof(int32_t) * (size_t)lay.Q * (size_t)lay.J_pad;
+    lay.b_x = lay.tc ? 0 : sizeof(int32_t) * (size_t)lay.Q * (size_t)lay.J_pad;
     lay.b_twid = nyq ? sizeof(float2) * lay.K : 0;
     lay.b_psi = d->input_kind == SRP_IN_STFT
                     ? sizeof(float2) * (size_t)lay.L_max * lay.Q * lay.Kb : 0;
@@ -258,43 +226,23 @@ void release(srp_plan_s *h) {
 }
 
 // Build the TDOA table in FP64 (Eq. Deltat_i / Eq. Deltat_i_spher), convert
-// x = Delta t fs to fixed point and upload it as [Q][J_pad].
+// x = Delta t fs to fixed point and upload it as [Q][J_pad]: int32 for the
+// CUDA-core kernels, or, for the tensor cores, (X, bits of sp) with
+// sp = (-1)^x0 sin(pi f) / pi for x = x0 + f decoded exactly as the kernel
+// decodes it (f = 0, an exact sample, is taken as 2^-40).  The candidates
+// are split over host threads.
 srp_status build_tdoa(const srp_plan_desc *d, srp_plan_s *h) {
     const Layout &lay = h->lay;
-    std::vector<int32_t> X((size_t)lay.Q * lay.J_pad, 0);
+    std::vector<int32_t> X;
+    std::vector<int2> xs;
+    if (lay.tc) xs.assign((size_t)lay.Q * lay.J_pad, make_int2(0, 0));
+    else X.assign((size_t)lay.Q * lay.J_pad, 0);
     const double scale = ldexp(1.0, lay.xf);
     const bool far = d->grid_kind == SRP_GRID_DIRECTIONS;
-    for (int64_t i = 0; i < lay.J; ++i) {
-        const double *g = d->grid_xyz + 3 * i;
-        double dist[kMaxM];
-        if (!far)
-            for (int m = 0; m < lay.M; ++m) {
-                const double *p = d->mic_xyz + 3 * m;
-                const double dx = p[0] - g[0], dy = p[1] - g[1], dz = p[2] - g[2];
-                dist[m] = sqrt(dx * dx + dy * dy + dz * dz);
-            }
-        for (int q = 0; q < lay.Q; ++q) {
-            const int m = lay.pm[q], mp = lay.pmp[q];
-            double dt;
-            if (far) {
-                const double *a = d->mic_xyz + 3 * m, *b = d->mic_xyz + 3 * mp;
-                dt = ((a[0] - b[0]) * g[0] + (a[1] - b[1]) * g[1] + (a[2] - b[2]) * g[2]) / d->c;
-            } else {
-                dt = (dist[m] - dist[mp]) / d->c;
-            }
-            X[(size_t)q * lay.J_pad + i] = (int32_t)llround(dt * d->fs * scale);
-        }
-    }
-    SRP_CUDA(cudaMemcpy(h->d_x, X.data(), lay.b_x, cudaMemcpyHostToDevice), "upload TDOA table");
-    if (!lay.tc) return SRP_OK;
-    // Tensor-core operand table: the same fixed-point TDOA with
-    // sp = (-1)^x0 sin(pi f) / pi for x = x0 + f, decoded exactly as the
-    // kernel decodes it; f = 0 (an exact sample) is taken as 2^-40.
-    std::vector<int2> xs((size_t)lay.Q * lay.J_pad);
     const double pi = 3.141592653589793238462643383279502884;
     const int32_t half = 1 << (lay.xf - 1);
-    for (size_t k = 0; k < xs.size(); ++k) {
-        const int32_t Xk = X[k];
+    // entry of a padding candidate (X = 0)
+    auto tc_entry = [&](int32_t Xk) {
         const int32_t x0 = (Xk + half) >> lay.xf;
         double f = ldexp((double)(Xk - x0 * (1 << lay.xf)), -lay.xf);
         if (f == 0.0) f = ldexp(1.0, -40);
@@ -302,7 +250,58 @@ srp_status build_tdoa(const srp_plan_desc *d, srp_plan_s *h) {
         if (x0 & 1) sp = -sp;
         int32_t bits;
         memcpy(&bits, &sp, sizeof bits);
-        xs[k] = make_int2(Xk, bits);
+        return make_int2(Xk, bits);
+    };
+    auto work = [&](int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i) {
+            double dist[kMaxM];
+            const double *g = i < lay.J ? d->grid_xyz + 3 * i : nullptr;
+            if (g != nullptr && !far)
+                for (int m = 0; m < lay.M; ++m) {
+                    const double *p = d->mic_xyz + 3 * m;
+                    const double dx = p[0] - g[0], dy = p[1] - g[1], dz = p[2] - g[2];
+                    dist[m] = sqrt(dx * dx + dy * dy + dz * dz);
+                }
+            for (int q = 0; q < lay.Q; ++q) {
+                int32_t Xk = 0;
+                if (g != nullptr) {
+                    const int m = lay.pm[q], mp = lay.pmp[q];
+                    double dt;
+                    if (far) {
+                        const double *a = d->mic_xyz + 3 * m, *b = d->mic_xyz + 3 * mp;
+                        dt = ((a[0] - b[0]) * g[0] + (a[1] - b[1]) * g[1] + (a[2] - b[2]) * g[2]) /
+                             d->c;
+                    } else {
+                        dt = (dist[m] - dist[mp]) / d->c;
+                    }
+                    Xk = (int32_t)llround(dt * d->fs * scale);
+                }
+                const size_t k = (size_t)q * lay.J_pad + i;
+                if (lay.tc) xs[k] = tc_entry(Xk);
+                else X[k] = Xk;
+            }
+        }
+    };
+    const int64_t work_items = lay.J_pad * (int64_t)lay.Q;
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 64u));
+    if (work_items < (1 << 16)) nt = 1;
+    if (nt == 1) {
+        work(0, lay.J_pad);
+    } else {
+        std::vector<std::thread> pool;
+        const int64_t per = (lay.J_pad + nt - 1) / nt;
+        for (unsigned t = 0; t < nt; ++t) {
+            const int64_t a = std::min<int64_t>(lay.J_pad, (int64_t)t * per);
+            const int64_t b = std::min<int64_t>(lay.J_pad, a + per);
+            if (a < b) pool.emplace_back(work, a, b);
+        }
+        for (auto &th : pool) th.join();
+    }
+    if (!lay.tc) {
+        SRP_CUDA(cudaMemcpy(h->d_x, X.data(), lay.b_x, cudaMemcpyHostToDevice),
+                 "upload TDOA table");
+        return SRP_OK;
     }
     SRP_CUDA(cudaMemcpy(h->d_xs, xs.data(), lay.b_xs, cudaMemcpyHostToDevice),
              "upload tensor-core TDOA table");
@@ -403,6 +402,16 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
 }  // namespace
 
 void set_error(const std::string &msg) { g_err = msg; }
+
+srp_status fail(srp_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+srp_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SRP_ERR_OOM : SRP_ERR_CUDA;
+}
 
 }  // namespace srp
 
@@ -527,7 +536,15 @@ srp_status srp_plan_tdoa(srp_handle h, double *x_host) {
     if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
     const Layout &L = h->lay;
     std::vector<int32_t> X((size_t)L.Q * L.J_pad);
-    SRP_CUDA(cudaMemcpy(X.data(), h->d_x, L.b_x, cudaMemcpyDeviceToHost), "download TDOA table");
+    if (L.tc) {
+        std::vector<int2> xs((size_t)L.Q * L.J_pad);
+        SRP_CUDA(cudaMemcpy(xs.data(), h->d_xs, L.b_xs, cudaMemcpyDeviceToHost),
+                 "download TDOA table");
+        for (size_t k = 0; k < xs.size(); ++k) X[k] = xs[k].x;
+    } else {
+        SRP_CUDA(cudaMemcpy(X.data(), h->d_x, L.b_x, cudaMemcpyDeviceToHost),
+                 "download TDOA table");
+    }
     const double inv = ldexp(1.0, -L.xf);
     for (int64_t i = 0; i < L.J; ++i)
         for (int q = 0; q < L.Q; ++q) x_host[i * L.Q + q] = X[(size_t)q * L.J_pad + i] * inv;

@@ -62,17 +62,34 @@ __device__ __forceinline__ void gcc_row(const float2 *tw, const float2 *ps, int 
     for (int t = warp; t <= 2 * nmax; t += nw) {
         const int n = t - nmax;
         const int nm = ((n % K) + K) % K;
+        // twiddle index k n mod K, stepped by 32 n mod K along the lane's bins
+        const int step = (int)((32ll * nm) % K);
+        int idx = (int)(((long long)lane * nm) % K);
         float acc = 0.0f;
         for (int k = lane; k < Kb; k += 32) {
-            const float2 w = tw[(k * nm) % K];
+            const float2 w = tw[idx];
             const float2 p = ps[k];
             acc = fmaf(p.x, w.x, acc);
             acc = fmaf(-p.y, w.y, acc);
+            idx += step;
+            if (idx >= K) idx -= K;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if (lane == 0) emit(t, n, acc * inv_k);
     }
+}
+
+// PHAT cross spectrum of one bin: u_m conj(u_m') with u = y / |y| (0 where
+// y = 0), which equals y_m y_m'^* / |y_m y_m'^*| without forming the product
+// of two small magnitudes.
+__device__ __forceinline__ float2 unit_phase(float2 v) {
+    const float a = hypotf(v.x, v.y);
+    return a > 0.0f ? make_float2(v.x / a, v.y / a) : make_float2(0.0f, 0.0f);
+}
+
+__device__ __forceinline__ float2 phat_cross(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
 // Stage one (frame, pair) spectrum row as a_k psi(k) and the twiddles.

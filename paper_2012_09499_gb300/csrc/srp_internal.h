@@ -81,6 +81,32 @@ struct srp_plan_s {
 namespace srp {
 
 void set_error(const std::string &msg);
+// Record msg (or the CUDA error text) for srp_last_error_message; return the status.
+srp_status fail(srp_status st, const std::string &msg);
+srp_status cuda_fail(cudaError_t e, const char *what);
+
+#define SRP_CUDA(call, what)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return srp::cuda_fail(e_, (what)); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 // ---- kernel launchers (srp_kernels.cu); each returns cudaGetLastError() ----
 cudaError_t launch_phat(const float2 *y, int L, int M, int Kb, const int2 *pairs, int Q,

@@ -33,11 +33,7 @@ __global__ void __launch_bounds__(256) k_phat(const float2 *__restrict__ y, int 
     for (int e = threadIdx.x; e < M * kPhatBins; e += blockDim.x) {
         const int m = e / kPhatBins, k = k0 + e % kPhatBins;
         float2 v = make_float2(0.0f, 0.0f);
-        if (k < Kb) {
-            v = y[((size_t)l * M + m) * Kb + k];
-            const float a = hypotf(v.x, v.y);
-            v = a > 0.0f ? make_float2(v.x / a, v.y / a) : make_float2(0.0f, 0.0f);
-        }
+        if (k < Kb) v = unit_phase(y[((size_t)l * M + m) * Kb + k]);
         u_sm[e] = v;
     }
     __syncthreads();
@@ -45,9 +41,8 @@ __global__ void __launch_bounds__(256) k_phat(const float2 *__restrict__ y, int 
         const int q = e / kPhatBins, kk = e % kPhatBins, k = k0 + kk;
         if (k >= Kb) continue;
         const int2 p = pairs[q];
-        const float2 a = u_sm[p.x * kPhatBins + kk], b = u_sm[p.y * kPhatBins + kk];
         psi[((size_t)l * Q + q) * Kb + k] =
-            make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+            phat_cross(u_sm[p.x * kPhatBins + kk], u_sm[p.y * kPhatBins + kk]);
     }
 }
 

@@ -1,0 +1,307 @@
+// Building blocks of the tensor-core (tcgen05 / TMEM / TMA) map kernels:
+// inline-PTX wrappers, bounded mbarrier waits, shared-memory descriptors, and
+// the on-chip generators of operand A (sinc weights of Eq. SRPapprox and the
+// steering matrix of Eq. GCC_IFT).  Included by srp_tc.cu (one plan per
+// launch) and srp_batch.cu (many plans in one persistent launch).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace srp {
+namespace tc {
+namespace {
+
+constexpr int kThreads = 224;        // warps 0-3: A generation + epilogue; 4: TMA; 5, 6: MMA
+constexpr int kTmaWarp = 4, kMmaWarp0 = 5;
+constexpr int kChunk = 64;           // lags per pipeline stage
+constexpr uint32_t kATile = 128u * 128u;  // 128 candidates x 64 lags x 2 B
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
+constexpr int kXRing = 8;            // (TDOA, sp) prefetch ring (slots per candidate row)
+constexpr int kXAhead = kXRing - 1;  // pairs in flight ahead of the current one
+constexpr int kMtStride = 130;       // floats per frame row of the epilogue tile
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_timer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(
+                     bar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One probe of the phase; a waiting thread is suspended in hardware (not
+// spinning) until the phase completes or the hint of 20 us runs out.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: gives up after kWaitLimitNs (or as soon as another thread of
+// the CTA gave up), records SRP timeout in *status and returns false.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                       int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_timer() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            atomicOr(status, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], "
+        "[%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 or FP16 in, FP32 accumulate).
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), tile base 1024-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Packed FP32 pairs (two lanes per instruction on sm_100+).
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 upk2(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+                 "r"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Weights of NG groups of 8 lags for one candidate row of the A tile(s):
+// w = sp / d with d = f + (mc - k) for lag slot k of the chunk, two lags per
+// reciprocal, written at row offset a_row with the 128-byte swizzle (chunk
+// position cc ^ sw).  With kSplit, the low part bf16(w - hi) goes to the tile
+// kATile bytes further on.
+template <int NG, bool kSplit, bool kHalf>
+__device__ __forceinline__ void gen_groups(uint32_t a_row, uint32_t sw, float f, float mc,
+                                           float sp) {
+    const uint64_t f2 = pk2(f, f);
+    const uint64_t two = pk2(2.0f, 2.0f);
+    // m2 = (mc - k - 1, mc - k): the second lag of a pair first, so that
+    // (db, da) * rr = (w_a, w_b) comes out in lag order
+    uint64_t m2 = pk2(mc - 1.0f, mc);
+#pragma unroll
+    for (int cc = 0; cc < NG; ++cc) {
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint64_t d2 = add2(f2, m2);  // (db, da), each rounded once
+            m2 = sub2(m2, two);
+            const float2 d = upk2(d2);
+            const float rr = sp * rcp_approx(d.x * d.y);
+            const float2 w = upk2(mul2(d2, pk2(rr, rr)));  // (w_a, w_b)
+            if (kHalf) {
+                hv[e] = pack_f16(w.x, w.y);
+            } else {
+                hv[e] = pack_bf16(w.x, w.y);
+                if (kSplit) {
+                    const uint64_t h2 = pk2(__uint_as_float(hv[e] << 16),
+                                            __uint_as_float(hv[e] & 0xFFFF0000u));
+                    const float2 lo = upk2(sub2(pk2(w.x, w.y), h2));
+                    lv[e] = pack_bf16(lo.x, lo.y);
+                }
+            }
+        }
+        const uint32_t off = a_row + (((uint32_t)cc ^ sw) << 4);
+        st_shared_v4(off, hv[0], hv[1], hv[2], hv[3]);
+        if (kSplit) st_shared_v4(off + kATile, lv[0], lv[1], lv[2], lv[3]);
+    }
+}
+
+// Steering weights of NG groups (4 bins each) for this thread's row: the
+// element pair (cos theta_k, -sin theta_k) of bins k0, k0 + 1, ..., i.e.
+// z = e^{-j theta_k}, starting from z0 and multiplied per bin by
+// w' = (p, q) = e^{-j 2 pi x / K}: z w' = (a p - b q, b p + a q) for z = (a, b).
+template <int NG, bool kSplit, bool kHalf>
+__device__ __forceinline__ void gen_steer(uint32_t a_row, uint32_t sw, float za, float zb,
+                                          float p, float q) {
+    uint64_t z = pk2(za, zb);
+    const uint64_t pp = pk2(p, p), qq = pk2(-q, q);
+#pragma unroll
+    for (int cc = 0; cc < NG; ++cc) {
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 v = upk2(z);
+            const uint64_t t = mul2(z, pp);
+            uint64_t zn;
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(zn) : "l"(pk2(v.y, v.x)), "l"(qq), "l"(t));
+            z = zn;
+            if (kHalf) {
+                hv[e] = pack_f16(v.x, v.y);
+            } else {
+                hv[e] = pack_bf16(v.x, v.y);
+                if (kSplit) {
+                    const uint64_t h2 = pk2(__uint_as_float(hv[e] << 16),
+                                            __uint_as_float(hv[e] & 0xFFFF0000u));
+                    const float2 lo = upk2(sub2(pk2(v.x, v.y), h2));
+                    lv[e] = pack_bf16(lo.x, lo.y);
+                }
+            }
+        }
+        const uint32_t off = a_row + (((uint32_t)cc ^ sw) << 4);
+        st_shared_v4(off, hv[0], hv[1], hv[2], hv[3]);
+        if (kSplit) st_shared_v4(off + kATile, lv[0], lv[1], lv[2], lv[3]);
+    }
+}
+
+}  // namespace
+}  // namespace tc
+}  // namespace srp

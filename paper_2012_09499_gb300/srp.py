@@ -52,6 +52,19 @@ class srp_plan_info(ctypes.Structure):
     ]
 
 
+class srp_batch_tiles(ctypes.Structure):
+    _fields_ = [("frames_per_tile", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+class srp_batch_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("items", ctypes.c_int32), ("ctas", ctypes.c_int32),
+        ("tiles", srp_batch_tiles), ("launches", ctypes.c_int32), ("tuned", ctypes.c_int32),
+        ("tuned_ms", ctypes.c_float), ("device_bytes", ctypes.c_size_t),
+    ]
+
+
 _lib = None
 
 
@@ -80,6 +93,13 @@ def lib():
             "srp_last_launch_count": [vp, ctypes.POINTER(i32)],
             "srp_destroy": [vp],
             "srp_poll_device_status": [vp, vp],
+            "srp_batch_create": [vp, i32, vp, ctypes.POINTER(vp)],
+            "srp_map_batch": [vp, vp, vp, vp, vp, vp, vp],
+            "srp_batch_tune": [vp, vp, vp, vp, vp, vp, vp],
+            "srp_batch_get_info": [vp, ctypes.POINTER(srp_batch_info)],
+            "srp_batch_stage_times": [vp, vp, i32],
+            "srp_batch_poll_device_status": [vp, vp],
+            "srp_batch_destroy": [vp],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -269,3 +289,115 @@ def srp_gcc_samples_static(M, K, n_aux, Nq, d_y, L, d_xi, stream=None):
     nq = np.ascontiguousarray(Nq, np.int32)
     _check(fn(int(M), int(K), int(n_aux), nq.ctypes.data, _ptr(d_y), int(L), _ptr(d_xi),
               _stream(stream)), "srp_gcc_samples_static")
+
+
+# --------------------------------------------------------------------------
+# batched uneven instances
+# --------------------------------------------------------------------------
+BATCH_STAGES = ("operands", "map", "argmax")
+
+
+def _ptr_array(items):
+    """ctypes array of device addresses (NULL for None)."""
+    arr = (ctypes.c_void_p * len(items))()
+    for k, t in enumerate(items):
+        arr[k] = _ptr(t)
+    return arr
+
+
+def srp_batch_create(handles, tiles=None):
+    """Batch over plan handles; tiles = (frames_per_tile, stages, ctas_per_sm),
+    zeros for defaults, or None."""
+    hs = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                            for h in handles])
+    t = None
+    if tiles is not None:
+        t = srp_batch_tiles(*[int(v) for v in tiles])
+    b = ctypes.c_void_p()
+    _check(lib().srp_batch_create(hs, len(handles), ctypes.byref(t) if t is not None else None,
+                                  ctypes.byref(b)), "srp_batch_create")
+    return b
+
+
+def _batch_args(d_in, L, d_maps, d_argmax, d_peak):
+    n = len(L)
+    Ls = (ctypes.c_int32 * n)(*[int(v) for v in L])
+    return (_ptr_array(d_in), Ls, None if d_maps is None else _ptr_array(d_maps),
+            _ptr_array(d_argmax), None if d_peak is None else _ptr_array(d_peak))
+
+
+def srp_map_batch(b, d_in, L, d_maps, d_argmax, d_peak=None, stream=None):
+    a = _batch_args(d_in, L, d_maps, d_argmax, d_peak)
+    _check(lib().srp_map_batch(b, *a, _stream(stream)), "srp_map_batch")
+
+
+def srp_batch_tune(b, d_in, L, d_maps, d_argmax, d_peak=None, stream=None):
+    a = _batch_args(d_in, L, d_maps, d_argmax, d_peak)
+    _check(lib().srp_batch_tune(b, *a, _stream(stream)), "srp_batch_tune")
+
+
+def srp_batch_get_info(b):
+    info = srp_batch_info()
+    _check(lib().srp_batch_get_info(b, ctypes.byref(info)), "srp_batch_get_info")
+    return info
+
+
+def srp_batch_stage_times(b):
+    ms = (ctypes.c_float * len(BATCH_STAGES))()
+    _check(lib().srp_batch_stage_times(b, ctypes.addressof(ms), len(BATCH_STAGES)),
+           "srp_batch_stage_times")
+    return dict(zip(BATCH_STAGES, list(ms)))
+
+
+def srp_batch_poll_device_status(b, stream=None):
+    _check(lib().srp_batch_poll_device_status(b, _stream(stream)), "srp_batch_poll_device_status")
+
+
+def srp_batch_destroy(b):
+    _check(lib().srp_batch_destroy(b), "srp_batch_destroy")
+
+
+class Batch:
+    """Owns one batch over Plan objects (kept alive with it); allocates
+    outputs with torch for convenience."""
+
+    def __init__(self, plans, tiles=None):
+        self.plans = list(plans)
+        self.handle = srp_batch_create([p.handle for p in self.plans], tiles)
+
+    @property
+    def info(self):
+        return srp_batch_get_info(self.handle)
+
+    def outputs(self, L, device, maps=True):
+        """Fresh per-plan (maps, argmax, peak) tensors for frame counts L."""
+        import torch
+        outs = []
+        for p, l in zip(self.plans, L):
+            outs.append((torch.empty((l, p.info.J), dtype=torch.float32, device=device)
+                         if maps else None,
+                         torch.empty(max(l, 1), dtype=torch.int32, device=device),
+                         torch.empty(max(l, 1), dtype=torch.float32, device=device)))
+        return outs
+
+    def map(self, d_in, L=None, outs=None, maps=True, stream=None, tune=False):
+        """Map every plan: d_in list of complex64 CUDA tensors (None where
+        L[i] = 0); returns the list of (maps or None, argmax, peak)."""
+        L = [x.shape[0] if x is not None else 0 for x in d_in] if L is None else list(L)
+        dev = next(x.device for x in d_in if x is not None)
+        outs = self.outputs(L, dev, maps) if outs is None else outs
+        fn = srp_batch_tune if tune else srp_map_batch
+        fn(self.handle, d_in, L, [o[0] for o in outs] if maps else None,
+           [o[1] for o in outs], [o[2] for o in outs], stream)
+        return outs
+
+    def close(self):
+        if self.handle is not None:
+            srp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

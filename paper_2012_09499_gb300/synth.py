@@ -203,3 +203,53 @@ def room_3d(seed: int = 0, L: int = 64, K: int = 1024, shape=(100, 80, 60),
     Y = free_field_stft(rng, mic, [src], 16000.0, K, L, snr_db)
     return dict(mic=mic, grid=grid, fs=16000.0, c=C_SOUND, K=K, L=L, Y=Y,
                 sources=src[None, :], far_field=False, name="room_3d")
+
+
+ROOM_MIX = np.array([6.0, 7.0, 3.5])  # the paper's room size (Sec. 4), candidates span it
+
+
+def uneven_instance(seed: int, J_range=(10_000, 500_000), L: int = 32, dims=None, M=None,
+                    K=None, aperture=None) -> dict:
+    """One array of the uneven batch mix: M uniform in {4..16} microphones
+    uniform in a cube of edge (aperture) uniform in [0.1, 1.0] m at the centre
+    of a 6 x 7 x 3.5 m room; K in {512, 1024, 2048} at fs = 16 kHz; a 2D
+    (horizontal plane through the array centre) or 3D candidate grid of cell
+    centres spanning the room with J log-uniform in J_range; one white
+    source at a uniform position (0.3 m from the walls; in the plane for 2D
+    grids) at SNR uniform in [0, 30] dB; L frames.  Keyword arguments fix a
+    draw."""
+    rng = np.random.default_rng(seed)
+    M = int(rng.integers(4, 17)) if M is None else int(M)
+    aperture = float(rng.uniform(0.1, 1.0)) if aperture is None else float(aperture)
+    K = int(rng.choice([512, 1024, 2048])) if K is None else int(K)
+    dims = int(rng.choice([2, 3])) if dims is None else int(dims)
+    lo, hi = J_range
+    J_target = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+    snr = float(rng.uniform(0.0, 30.0))
+    centre = ROOM_MIX / 2.0
+    mic = random_cube_array(rng, M, aperture, centre)
+    if dims == 2:
+        nx = max(2, int(round(np.sqrt(J_target * ROOM_MIX[0] / ROOM_MIX[1]))))
+        ny = max(2, int(round(J_target / nx)))
+        sp = np.array([ROOM_MIX[0] / nx, ROOM_MIX[1] / ny])
+        gx = (np.arange(nx) + 0.5) * sp[0]
+        gy = (np.arange(ny) + 0.5) * sp[1]
+        X, Yg = np.meshgrid(gx, gy, indexing="ij")
+        grid = np.stack([X.ravel(), Yg.ravel(), np.full(X.size, centre[2])], axis=1)
+        src = np.array([*rng.uniform(0.3, ROOM_MIX[:2] - 0.3), centre[2]])
+    else:
+        s = (J_target / float(np.prod(ROOM_MIX))) ** (1.0 / 3.0)
+        shape = tuple(max(2, int(round(v * s))) for v in ROOM_MIX)
+        axes = [(np.arange(shape[d]) + 0.5) * ROOM_MIX[d] / shape[d] for d in range(3)]
+        gx, gy, gz = np.meshgrid(*axes, indexing="ij")
+        grid = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1)
+        src = rng.uniform(0.3, ROOM_MIX - 0.3)
+    Y = free_field_stft(rng, mic, [src], 16000.0, K, L, snr)
+    return dict(mic=mic, grid=grid, fs=16000.0, c=C_SOUND, K=K, L=L, Y=Y,
+                sources=src[None, :], far_field=False, snr_db=snr, aperture=aperture,
+                dims=dims, name="uneven")
+
+
+def uneven_mix(seed: int, n: int, J_range=(10_000, 500_000), L: int = 32) -> list:
+    """n arrays of the uneven mix (uneven_instance with seeds derived from seed)."""
+    return [uneven_instance(seed * 100_003 + i, J_range, L) for i in range(n)]

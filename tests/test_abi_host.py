@@ -93,23 +93,24 @@ def test_footprint_counts_every_buffer():
     assert fp == info.device_bytes
     Q, Jp, Lp = 28, 1024, 64
     Sc = int(np.sum(-(-(2 * nq + 5) // 64) * 64))  # each pair padded to 64-lag chunks
-    common = 4 + 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
+    # status, pairs, N_q, pair offsets, cross spectra, argmax partials
+    common = 4 + 8 * Q + 4 * Q + 4 * Q + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
+    x_tab = 4 * Q * Jp  # int32 TDOA table of the CUDA-core kernels
     # tensor-core engine: twiddles, 8-aligned pair offsets, split 16-bit GCC samples
     tc_tables = 4 * Q + 8 * Q * Jp + 16 * (Sc // 64)  # pair offsets, (TDOA, sp), chunk table
     assert fp == common + 8 * 1024 + tc_tables + 2 * 2 * Lp * Sc
     d3, keep3 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, engine="cuda_cores")
     Sp = -(-info.S // 64) * 64
-    assert srp.srp_plan_footprint(d3) == common + 8 * 1024 + 4 * Sp * Lp
+    assert srp.srp_plan_footprint(d3) == common + x_tab + 8 * 1024 + 4 * Sp * Lp
     d4, keep4 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision="bf16")
     assert srp.srp_plan_footprint(d4) == common + 8 * 1024 + tc_tables + 2 * Lp * Sc
-    base = 4 + 8 * Q + 4 * Q + 4 * Q + 4 * Q * Jp + 8 * 64 * Q * 513 + 8 * Lp * (Jp // 128)
     d2, keep2 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional",
                       engine="cuda_cores")
-    assert srp.srp_plan_footprint(d2) == base
+    assert srp.srp_plan_footprint(d2) == common + x_tab
     # conventional on the tensor cores: 2 Kb = 1026 slots per pair, padded to 1088
     Scc = Q * 1088
     d5, keep5 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional")
-    assert srp.srp_plan_footprint(d5) == (base + 4 * Q + 8 * Q * Jp + 16 * (Scc // 64)
+    assert srp.srp_plan_footprint(d5) == (common + 4 * Q + 8 * Q * Jp + 16 * (Scc // 64)
                                           + 2 * 2 * Lp * Scc)
 
 
@@ -166,3 +167,17 @@ def test_engine_choice_by_accumulation_bias():
         assert info.tensor_cores == tc, (mic.shape[0], K, mode, prec)
     d, keep = srp.make_desc(mic8, grid, 16000.0, 343.0, 1024, engine="cuda_cores")
     assert srp.srp_plan_describe(d)[0].tensor_cores == 0
+
+
+def test_batch_entry_points_reject_bad_arguments():
+    """Argument checks of the batch entry points run before any CUDA call."""
+    L = srp.lib()
+    out = ctypes.c_void_p()
+    assert L.srp_batch_create(None, 0, None, ctypes.byref(out)) == srp.SRP_ERR_INVALID_ARG
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.srp_batch_create(arr, 2, None, ctypes.byref(out)) == srp.SRP_ERR_INVALID_ARG
+    assert L.srp_batch_create(arr, 1, None, None) == srp.SRP_ERR_INVALID_ARG
+    assert L.srp_map_batch(None, None, None, None, None, None, None) == srp.SRP_ERR_INVALID_ARG
+    info = srp.srp_batch_info()
+    assert L.srp_batch_get_info(None, ctypes.byref(info)) == srp.SRP_ERR_INVALID_ARG
+    assert L.srp_batch_destroy(None) == srp.SRP_OK

@@ -1,0 +1,193 @@
+"""Batched uneven instances through the C ABI: srp_map_batch over plans with
+different M, J, K and grids must give, for every plan, the map srp_map
+defines, within the same tolerances against the FP64 oracle (FP32 path:
+1e-4 x peak, argmax exact except documented ties; BF16/FP16: 1e-2 x peak).
+Frame counts vary per plan and per call, including plans skipped (L = 0)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2012_09499_gb300 import build_lib, srp, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-4, "bf16": 1e-2, "fp16": 1e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build_lib.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def small_mix(seed, n, J_range, L, **fix):
+    return [synth.uneven_instance(seed * 1000 + i, J_range, L, **fix) for i in range(n)]
+
+
+def make_plans(cfgs, mode, precision, max_frames):
+    return [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], mode=mode, n_aux=2,
+                     precision=precision, max_frames=max_frames) for c in cfgs]
+
+
+def oracle_maps(cfg, mode, L, sub=None):
+    grid = cfg["grid"] if sub is None else cfg["grid"][sub]
+    maps, _, _ = oracle.srp_map(cfg["Y"][:L], cfg["mic"], grid, cfg["fs"], cfg["c"], cfg["K"],
+                                mode=mode, n_aux=2)
+    return maps
+
+
+def check(maps, idx, peak, ref, tol, exact_argmax=True):
+    pk = np.abs(ref).max(axis=1)
+    err = np.abs(maps.astype(np.float64) - ref).max(axis=1)
+    assert np.all(err <= tol * pk), (err / pk).max()
+    assert np.array_equal(idx, np.argmax(maps, axis=1))  # first maximiser of its own map
+    assert np.array_equal(peak, maps[np.arange(maps.shape[0]), idx])
+    if exact_argmax:
+        ridx = np.argmax(ref, axis=1)
+        for l in np.nonzero(idx != ridx)[0]:  # documented ties only
+            assert ref[l, ridx[l]] - ref[l, idx[l]] <= 2 * tol * pk[l]
+    return (err / pk).max()
+
+
+def run_batch(batch, cfgs, L, tune=False):
+    d_in = [dev(c["Y"][:l]) if l > 0 else None for c, l in zip(cfgs, L)]
+    outs = batch.map(d_in, L=L, tune=tune)
+    torch.cuda.synchronize()
+    srp.srp_batch_poll_device_status(batch.handle)
+    return [(m.cpu().numpy(), a.cpu().numpy()[:l], p.cpu().numpy()[:l])
+            for (m, a, p), l in zip(outs, L)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+def test_nyquist_batch_matches_oracle(precision):
+    cfgs = small_mix(1, 5, (800, 4000), 32)
+    plans = make_plans(cfgs, "nyquist", precision, 32)
+    batch = srp.Batch(plans)
+    L = [32, 17, 0, 5, 32]
+    res = run_batch(batch, cfgs, L)
+    for c, (m, a, p), l in zip(cfgs, res, L):
+        if l == 0:
+            continue
+        check(m, a, p, oracle_maps(c, "nyquist", l), TOL[precision],
+              exact_argmax=precision == "fp32")
+    batch.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_conventional_batch_matches_oracle(precision):
+    # few pairs and bins, so that the FP32 plans run on the tensor cores
+    cfgs = [synth.uneven_instance(50 + i, (600, 1500), 6, M=M, K=K)
+            for i, (M, K) in enumerate([(4, 512), (6, 1024), (5, 2048), (4, 1024)])]
+    plans = make_plans(cfgs, "conventional", precision, 8)
+    assert all(p.info.tensor_cores == 1 for p in plans)
+    batch = srp.Batch(plans)
+    L = [6, 3, 6, 1]
+    res = run_batch(batch, cfgs, L)
+    for c, (m, a, p), l in zip(cfgs, res, L):
+        check(m, a, p, oracle_maps(c, "conventional", l), TOL[precision],
+              exact_argmax=precision == "fp32")
+    batch.close()
+
+
+def test_batch_equals_per_plan_map():
+    cfgs = small_mix(2, 4, (2000, 9000), 16)
+    plans = make_plans(cfgs, "nyquist", "fp32", 16)
+    batch = srp.Batch(plans)
+    L = [16, 9, 16, 3]
+    res = run_batch(batch, cfgs, L)
+    for c, pl, (m, a, p), l in zip(cfgs, plans, res, L):
+        m1, a1, p1 = pl.map(dev(c["Y"][:l]), L=l)
+        torch.cuda.synchronize()
+        m1 = m1.cpu().numpy()
+        pk = np.abs(m1).max(axis=1)
+        assert np.all(np.abs(m - m1).max(axis=1) <= 1e-6 * pk)
+    batch.close()
+
+
+def test_batch_repeated_calls_and_varying_frames():
+    cfgs = small_mix(3, 3, (1000, 3000), 24)
+    plans = make_plans(cfgs, "nyquist", "bf16", 24)
+    batch = srp.Batch(plans)
+    first = run_batch(batch, cfgs, [24, 24, 24])
+    again = run_batch(batch, cfgs, [24, 24, 24])
+    for (m0, a0, p0), (m1, a1, p1) in zip(first, again):
+        assert np.array_equal(m0, m1) and np.array_equal(a0, a1)
+    # fewer frames, one plan skipped: the leading frames are unchanged
+    part = run_batch(batch, cfgs, [7, 0, 13])
+    for (m0, a0, _), (m1, a1, _), l in zip(first, part, [7, 0, 13]):
+        assert np.array_equal(m0[:l], m1) and np.array_equal(a0[:l], a1)
+    batch.close()
+
+
+def test_batch_tuner_and_explicit_tiles():
+    cfgs = small_mix(4, 4, (3000, 12000), 32)
+    plans = make_plans(cfgs, "nyquist", "fp32", 32)
+    batch = srp.Batch(plans)
+    L = [32, 32, 20, 32]
+    res = run_batch(batch, cfgs, L, tune=True)
+    info = batch.info
+    assert info.tuned == 1 and info.tuned_ms > 0.0 and info.launches == 3
+    assert info.tiles.frames_per_tile in (16, 32)
+    refs = [oracle_maps(c, "nyquist", l) for c, l in zip(cfgs, L)]
+    for (m, a, p), ref in zip(res, refs):
+        check(m, a, p, ref, TOL["fp32"])
+    # the chosen tiles keep serving ordinary calls
+    for (m, a, p), ref in zip(run_batch(batch, cfgs, L), refs):
+        check(m, a, p, ref, TOL["fp32"])
+    batch.close()
+    # a fixed tile shape: 16 frames per item, two stages, one CTA per SM
+    b2 = srp.Batch(plans, tiles=(16, 2, 1))
+    assert (b2.info.tiles.frames_per_tile, b2.info.tiles.stages,
+            b2.info.tiles.ctas_per_sm) == (16, 2, 1)
+    for (m, a, p), ref in zip(run_batch(b2, cfgs, L), refs):
+        check(m, a, p, ref, TOL["fp32"])
+    b2.close()
+
+
+def test_batch_full_scale_sampled():
+    """Arrays of the uneven mix at full size (J up to 500k, K up to 2048,
+    M up to 16): sampled candidates and frames against the oracle."""
+    cfgs = synth.uneven_mix(7, 6, L=32)
+    plans = make_plans(cfgs, "nyquist", "fp32", 32)
+    batch = srp.Batch(plans)
+    L = [32] * len(cfgs)
+    d_in = [dev(c["Y"]) for c in cfgs]
+    outs = batch.map(d_in, L=L)
+    torch.cuda.synchronize()
+    srp.srp_batch_poll_device_status(batch.handle)
+    for c, (m, a, p) in zip(cfgs, outs):
+        J = c["grid"].shape[0]
+        sub = np.arange(0, J, max(1, J // 1500))
+        frames = [0, 31]
+        ref = np.stack([oracle_maps({**c, "Y": c["Y"][[f]]}, "nyquist", 1, sub)[0]
+                        for f in frames])
+        got = m[frames][:, sub].cpu().numpy().astype(np.float64)
+        full = m[frames].cpu().numpy()
+        pk = np.abs(full).max(axis=1)
+        assert np.all(np.abs(got - ref).max(axis=1) <= TOL["fp32"] * pk)
+        assert np.array_equal(a[frames].cpu().numpy(), np.argmax(full, axis=1))
+    batch.close()
+
+
+def test_batch_rejects_mixed_modes_and_cuda_core_plans():
+    cfgs = small_mix(5, 2, (500, 800), 4)
+    a = make_plans(cfgs[:1], "nyquist", "fp32", 4)[0]
+    b = make_plans(cfgs[1:], "conventional", "fp32", 4)[0]
+    with pytest.raises(srp.SrpError) as e:
+        srp.Batch([a, b])
+    assert e.value.status == srp.SRP_ERR_UNSUPPORTED
+    c = srp.Plan(cfgs[0]["mic"], cfgs[0]["grid"], 16000.0, 343.0, cfgs[0]["K"],
+                 engine="cuda_cores", max_frames=4)
+    with pytest.raises(srp.SrpError) as e:
+        srp.Batch([a, c])
+    assert e.value.status == srp.SRP_ERR_UNSUPPORTED
+    batch = srp.Batch([a])
+    with pytest.raises(srp.SrpError) as e:  # more frames than the plan takes
+        srp.srp_map_batch(batch.handle, [None], [5], None, [None])
+    assert e.value.status == srp.SRP_ERR_INVALID_ARG
+    batch.close()
