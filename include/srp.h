@@ -296,9 +296,12 @@ SRP_API srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const in
 
 SRP_API srp_status srp_batch_get_info(srp_batch b, srp_batch_info *info);
 
-/* Milliseconds of the last call's three kernels in ms[0..n): 0 operands
- * (cross spectra and GCC samples or bin operands), 1 map contraction,
- * 2 argmax.  Waits for the last call to finish.                           */
+/* Per-kernel timing: while enabled, srp_map_batch launches the same three
+ * kernels directly instead of through the graph, with CUDA events around
+ * each; srp_batch_stage_times waits for the last call and returns its
+ * milliseconds in ms[0..n): 0 operands (cross spectra and GCC samples or
+ * bin operands), 1 map contraction, 2 argmax.                              */
+SRP_API srp_status srp_batch_set_timing(srp_batch b, int32_t enable);
 SRP_API srp_status srp_batch_stage_times(srp_batch b, float *ms, int32_t n);
 
 /* As srp_poll_device_status, for the batch's kernels.                      */
@@ -306,6 +309,81 @@ SRP_API srp_status srp_batch_poll_device_status(srp_batch b, srp_stream_t s);
 
 /* Release the batch (not its plans).  NULL is a no-op.                    */
 SRP_API srp_status srp_batch_destroy(srp_batch b);
+
+/* ------------------------------------------------------------------------
+ * Serving: many arrays (streams, one resident plan each) whose frame blocks
+ * arrive over time, mapped by continuous batching.  The paper has no
+ * counterpart; each result is the map, argmax and peak srp_map defines for
+ * the request's frames alone.
+ *
+ * A worker thread forms iterations: each stream's queued requests, in
+ * arrival order and up to the plan's max_frames, become one group of
+ * consecutive frames; the groups of an iteration are mapped together (one
+ * srp_map_batch launch over the tensor-core plans of one mode and precision,
+ * srp_map for every other plan).  Up to max_inflight iterations are on the
+ * GPU at once, each on its own CUDA stream, so requests that arrive while
+ * others run join the next iteration as soon as a slot and memory free up,
+ * and its copies and kernels overlap the running ones.  Admission is by
+ * device memory: each group's inputs, maps, argmax and peak are carved from
+ * one device arena of device_budget_bytes; a group that does not fit waits
+ * for earlier ones to finish.  The plans must outlive the server.
+ * ------------------------------------------------------------------------ */
+typedef struct srp_server_s *srp_server;
+
+typedef struct {
+    size_t device_budget_bytes; /* device arena for the requests in flight (> 0) */
+    size_t host_budget_bytes;   /* pinned host staging for queued and in-flight requests (> 0) */
+    int32_t max_inflight;       /* iterations on the GPU at once, 1..8 */
+    int32_t no_batching;        /* nonzero: every plan maps with its own srp_map call */
+} srp_server_desc;
+
+/* One finished request.  Times are milliseconds since srp_server_create on
+ * the host's steady clock: submission, start of its iteration, and the
+ * moment its results were in the caller's buffers.                       */
+typedef struct {
+    uint64_t request_id, tag;
+    int32_t stream, L;
+    int32_t status;             /* SRP_OK, SRP_ERR_TIMEOUT (deadline passed before it
+                                   started) or the error of its iteration */
+    double t_submit_ms, t_start_ms, t_done_ms;
+} srp_completion;
+
+typedef struct {
+    int64_t submitted, completed, frames_completed, rejected, timed_out, failed;
+    int64_t iterations, kernel_launches, admission_waits, queued;
+    size_t device_budget_bytes, device_bytes_in_use, device_bytes_peak;
+    int32_t batched_streams;    /* streams mapped by the batched launch */
+} srp_server_stats;
+
+/* Start a server over n plans (stream i maps with plans[i]).  Allocates the
+ * device arena, the pinned staging, max_inflight CUDA streams and (when two
+ * or more plans share a tensor-core mode and precision) one batch per
+ * in-flight slot, and starts the worker thread.                          */
+SRP_API srp_status srp_server_create(const srp_handle *plans, int32_t n,
+                                     const srp_server_desc *d, srp_server *out);
+
+/* Queue L frames (1 <= L <= max_frames of the stream's plan) of host input
+ * h_in in the plan's input_kind layout; it is copied before this returns.
+ * Results go to host h_argmax [L] (required), h_peak [L] and h_maps [L][J]
+ * (optional; pinned memory keeps the maps copy asynchronous), which must stay
+ * valid until the request's completion is polled.  deadline_ms > 0: a
+ * request not started within that many ms completes with SRP_ERR_TIMEOUT.
+ * Returns SRP_ERR_OOM (and queues nothing) when the request alone exceeds
+ * the device budget or the pinned staging is full.                      */
+SRP_API srp_status srp_server_submit(srp_server s, int32_t stream, const void *h_in, int32_t L,
+                                     int32_t *h_argmax, float *h_peak, float *h_maps,
+                                     uint64_t tag, double deadline_ms, uint64_t *request_id);
+
+/* Move up to max finished requests into out (oldest first); *n_out is the
+ * count.  wait_ms > 0 waits up to that long for one to finish.            */
+SRP_API srp_status srp_server_poll(srp_server s, srp_completion *out, int32_t max,
+                                   int32_t *n_out, int32_t wait_ms);
+
+SRP_API srp_status srp_server_get_stats(srp_server s, srp_server_stats *st);
+
+/* Finish every queued request, stop the worker and release the server (not
+ * its plans).  Completions not yet polled are dropped.  NULL is a no-op.  */
+SRP_API srp_status srp_server_destroy(srp_server s);
 
 /* Static description of a status code.                                    */
 SRP_API const char *srp_status_string(srp_status s);

@@ -629,6 +629,12 @@ struct srp_batch_s {
     size_t part_bytes = 0;
     int *d_status = nullptr;
     alignas(64) unsigned char b_map[128] = {};
+    // the three kernels of a call, as captured in the graph
+    void (*operands)(const BatchInst *, const BatchCall *, int, uint16_t *) = nullptr;
+    void (*persist)(const CUtensorMap, const PersistArgs) = nullptr;
+    size_t op_smem = 0, persist_smem_bytes = 0;
+    PersistArgs pargs = {};
+    int timing = 0;  // calls launch the kernels directly, with events between them
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -667,6 +673,21 @@ cudaError_t grow(T **p, size_t &cap, size_t bytes) {
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
     if (e == cudaSuccess) cap = bytes;
     return e;
+}
+
+// The three kernels of a call on stream s (captured into the graph, or
+// launched directly with events around each when timing).
+cudaError_t enqueue_kernels(srp_batch_s *b, cudaStream_t s, bool timed) {
+    const int n = (int)b->plans.size();
+    const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(b->b_map);
+    if (timed) cudaEventRecord(b->ev[0], s);
+    b->operands<<<(unsigned)b->op_blocks, 128, b->op_smem, s>>>(b->d_inst, b->d_call, n, b->d_b);
+    if (timed) cudaEventRecord(b->ev[1], s);
+    b->persist<<<(unsigned)b->n_ctas, kThreads, b->persist_smem_bytes, s>>>(map, b->pargs);
+    if (timed) cudaEventRecord(b->ev[2], s);
+    k_batch_argmax<<<(unsigned)b->frame_blocks, 256, 0, s>>>(b->d_inst, b->d_call, n);
+    if (timed) cudaEventRecord(b->ev[3], s);
+    return cudaGetLastError();
 }
 
 // Lay out operand B, the work list and its schedule for tile choice t, upload
@@ -785,20 +806,17 @@ srp_status batch_configure(srp_batch_s *b, const TileChoice &t) {
     SRP_CUDA(cudaFuncSetAttribute(operands, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)std::max<size_t>(op_smem, 1)), "operand kernel attribute");
 
+    b->operands = operands;
+    b->persist = persist;
+    b->op_smem = op_smem;
+    b->persist_smem_bytes = smem;
+    b->pargs = pa;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
-    const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(b->b_map);
     SRP_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin graph capture");
-    cudaEventRecord(b->ev[0], b->cap);
-    operands<<<(unsigned)op, 128, op_smem, b->cap>>>(b->d_inst, b->d_call, n, b->d_b);
-    cudaEventRecord(b->ev[1], b->cap);
-    persist<<<(unsigned)ctas, kThreads, smem, b->cap>>>(map, pa);
-    cudaEventRecord(b->ev[2], b->cap);
-    k_batch_argmax<<<(unsigned)fr, 256, 0, b->cap>>>(b->d_inst, b->d_call, n);
-    cudaEventRecord(b->ev[3], b->cap);
-    cudaError_t launch_err = cudaGetLastError();
+    cudaError_t launch_err = enqueue_kernels(b, b->cap, false);
     cudaError_t cap_err = cudaStreamEndCapture(b->cap, &b->graph);
     if (launch_err != cudaSuccess) return cuda_fail(launch_err, "capture batch kernels");
     if (cap_err != cudaSuccess) return cuda_fail(cap_err, "end graph capture");
@@ -837,7 +855,11 @@ srp_status batch_launch(srp_batch_s *b, cudaStream_t s) {
     SRP_CUDA(cudaMemcpyAsync(b->d_call, b->h_call, sizeof(BatchCall) * b->plans.size(),
                              cudaMemcpyHostToDevice, s), "upload batch call table");
     SRP_CUDA(cudaEventRecord(b->copied, s), "record batch event");
-    SRP_CUDA(cudaGraphLaunch(b->exec, s), "launch batch graph");
+    if (b->timing) {
+        SRP_CUDA(enqueue_kernels(b, s, true), "launch batch kernels");
+    } else {
+        SRP_CUDA(cudaGraphLaunch(b->exec, s), "launch batch graph");
+    }
     return SRP_OK;
 }
 
@@ -1055,8 +1077,15 @@ srp_status srp_batch_get_info(srp_batch b, srp_batch_info *info) {
     return SRP_OK;
 }
 
+srp_status srp_batch_set_timing(srp_batch b, int32_t enable) {
+    if (b == nullptr) return fail(SRP_ERR_INVALID_ARG, "batch is NULL");
+    b->timing = enable ? 1 : 0;
+    return SRP_OK;
+}
+
 srp_status srp_batch_stage_times(srp_batch b, float *ms, int32_t n) {
     if (b == nullptr || ms == nullptr || n < 0) return fail(SRP_ERR_INVALID_ARG, "bad argument");
+    if (!b->timing) return fail(SRP_ERR_INVALID_ARG, "timing is off (srp_batch_set_timing)");
     DeviceGuard g(b->device);
     if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the batch's device");
     SRP_CUDA(cudaEventSynchronize(b->ev[3]), "wait for the batch call");

@@ -65,6 +65,26 @@ class srp_batch_info(ctypes.Structure):
     ]
 
 
+class srp_server_desc(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_size_t), ("host_budget_bytes", ctypes.c_size_t),
+                ("max_inflight", ctypes.c_int32), ("no_batching", ctypes.c_int32)]
+
+
+class srp_completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("tag", ctypes.c_uint64),
+                ("stream", ctypes.c_int32), ("L", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double)]
+
+
+class srp_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "submitted", "completed", "frames_completed", "rejected", "timed_out", "failed",
+        "iterations", "kernel_launches", "admission_waits", "queued")] + [
+        ("device_budget_bytes", ctypes.c_size_t), ("device_bytes_in_use", ctypes.c_size_t),
+        ("device_bytes_peak", ctypes.c_size_t), ("batched_streams", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -98,8 +118,15 @@ def lib():
             "srp_batch_tune": [vp, vp, vp, vp, vp, vp, vp],
             "srp_batch_get_info": [vp, ctypes.POINTER(srp_batch_info)],
             "srp_batch_stage_times": [vp, vp, i32],
+            "srp_batch_set_timing": [vp, i32],
             "srp_batch_poll_device_status": [vp, vp],
             "srp_batch_destroy": [vp],
+            "srp_server_create": [vp, i32, ctypes.POINTER(srp_server_desc), ctypes.POINTER(vp)],
+            "srp_server_submit": [vp, i32, vp, i32, vp, vp, vp, ctypes.c_uint64, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_uint64)],
+            "srp_server_poll": [vp, vp, i32, ctypes.POINTER(i32), i32],
+            "srp_server_get_stats": [vp, ctypes.POINTER(srp_server_stats)],
+            "srp_server_destroy": [vp],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -342,6 +369,10 @@ def srp_batch_get_info(b):
     return info
 
 
+def srp_batch_set_timing(b, enable=True):
+    _check(lib().srp_batch_set_timing(b, 1 if enable else 0), "srp_batch_set_timing")
+
+
 def srp_batch_stage_times(b):
     ms = (ctypes.c_float * len(BATCH_STAGES))()
     _check(lib().srp_batch_stage_times(b, ctypes.addressof(ms), len(BATCH_STAGES)),
@@ -401,3 +432,87 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------
+# serving
+# --------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching server over Plan objects (stream i maps with
+    plans[i]).  submit() copies the input frames at once; results land in
+    numpy arrays owned by this object and are returned by poll()."""
+
+    def __init__(self, plans, device_budget_bytes, host_budget_bytes=256 << 20, max_inflight=2,
+                 batching=True):
+        self.plans = list(plans)
+        d = srp_server_desc(int(device_budget_bytes), int(host_budget_bytes), int(max_inflight),
+                            0 if batching else 1)
+        hs = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib().srp_server_create(hs, len(self.plans), ctypes.byref(d), ctypes.byref(h)),
+               "srp_server_create")
+        self.handle = h
+        self._pending = {}  # request id -> (argmax, peak, maps) buffers
+        self._buf = (srp_completion * 256)()
+
+    def submit(self, stream, frames, tag=0, want_maps=False, deadline_ms=0.0):
+        """Queue frames (complex64 [L][M][Kb] numpy array); returns the request id."""
+        x = np.ascontiguousarray(frames, np.complex64)
+        L = x.shape[0]
+        am = np.empty(L, np.int32)
+        pk = np.empty(L, np.float32)
+        mp = np.empty((L, self.plans[stream].info.J), np.float32) if want_maps else None
+        rid = ctypes.c_uint64()
+        _check(lib().srp_server_submit(self.handle, int(stream), x.ctypes.data, L, am.ctypes.data,
+                                       pk.ctypes.data, None if mp is None else mp.ctypes.data,
+                                       int(tag), float(deadline_ms), ctypes.byref(rid)),
+               "srp_server_submit")
+        self._pending[rid.value] = (am, pk, mp)
+        return rid.value
+
+    def poll(self, wait_ms=0):
+        """Finished requests as dicts (id, tag, stream, L, status, times and
+        the result arrays)."""
+        n = ctypes.c_int32()
+        _check(lib().srp_server_poll(self.handle, self._buf, len(self._buf), ctypes.byref(n),
+                                     int(wait_ms)), "srp_server_poll")
+        out = []
+        for c in self._buf[: n.value]:
+            am, pk, mp = self._pending.pop(c.request_id)
+            out.append(dict(id=c.request_id, tag=c.tag, stream=c.stream, L=c.L, status=c.status,
+                            t_submit=c.t_submit_ms, t_start=c.t_start_ms, t_done=c.t_done_ms,
+                            argmax=am, peak=pk, maps=mp))
+        return out
+
+    def drain(self, timeout_s=60.0):
+        """Poll until every submitted request has finished."""
+        import time
+        out = []
+        t_end = time.monotonic() + timeout_s
+        while self._pending and time.monotonic() < t_end:
+            out += self.poll(wait_ms=50)
+        if self._pending:
+            raise TimeoutError(f"{len(self._pending)} requests still pending")
+        return out
+
+    @property
+    def stats(self):
+        st = srp_server_stats()
+        _check(lib().srp_server_get_stats(self.handle, ctypes.byref(st)), "srp_server_get_stats")
+        return st
+
+    def close(self):
+        if self.handle is not None:
+            srp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def srp_server_destroy(h):
+    _check(lib().srp_server_destroy(h), "srp_server_destroy")

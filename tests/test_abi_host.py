@@ -181,3 +181,26 @@ def test_batch_entry_points_reject_bad_arguments():
     info = srp.srp_batch_info()
     assert L.srp_batch_get_info(None, ctypes.byref(info)) == srp.SRP_ERR_INVALID_ARG
     assert L.srp_batch_destroy(None) == srp.SRP_OK
+
+
+def test_server_entry_points_reject_bad_arguments():
+    """Argument checks of the serving entry points run before any CUDA call."""
+    L = srp.lib()
+    out = ctypes.c_void_p()
+    d = srp.srp_server_desc(1 << 20, 1 << 20, 2, 0)
+    assert L.srp_server_create(None, 0, ctypes.byref(d), ctypes.byref(out)) == \
+        srp.SRP_ERR_INVALID_ARG
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.srp_server_create(arr, 1, ctypes.byref(d), ctypes.byref(out)) == \
+        srp.SRP_ERR_INVALID_ARG
+    bad = srp.srp_server_desc(0, 1 << 20, 2, 0)
+    assert L.srp_server_create(arr, 1, ctypes.byref(bad), ctypes.byref(out)) == \
+        srp.SRP_ERR_INVALID_ARG
+    bad = srp.srp_server_desc(1 << 20, 1 << 20, 9, 0)
+    assert L.srp_server_create(arr, 1, ctypes.byref(bad), ctypes.byref(out)) == \
+        srp.SRP_ERR_INVALID_ARG
+    n = ctypes.c_int32()
+    assert L.srp_server_poll(None, None, 0, ctypes.byref(n), 0) == srp.SRP_ERR_INVALID_ARG
+    assert L.srp_server_submit(None, 0, None, 1, None, None, None, 0, 0.0, None) == \
+        srp.SRP_ERR_INVALID_ARG
+    assert L.srp_server_destroy(None) == srp.SRP_OK

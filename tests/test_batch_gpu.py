@@ -191,3 +191,20 @@ def test_batch_rejects_mixed_modes_and_cuda_core_plans():
         srp.srp_map_batch(batch.handle, [None], [5], None, [None])
     assert e.value.status == srp.SRP_ERR_INVALID_ARG
     batch.close()
+
+
+def test_batch_timing_mode_same_outputs():
+    cfgs = small_mix(6, 3, (1000, 3000), 16)
+    plans = make_plans(cfgs, "nyquist", "fp32", 16)
+    batch = srp.Batch(plans)
+    L = [16, 8, 16]
+    graph = run_batch(batch, cfgs, L)
+    with pytest.raises(srp.SrpError):
+        srp.srp_batch_stage_times(batch.handle)  # timing is off
+    srp.srp_batch_set_timing(batch.handle, True)
+    timed = run_batch(batch, cfgs, L)
+    st = srp.srp_batch_stage_times(batch.handle)
+    assert all(v > 0.0 for v in st.values()), st
+    for (m0, a0, _), (m1, a1, _) in zip(graph, timed):
+        assert np.array_equal(m0, m1) and np.array_equal(a0, a1)
+    batch.close()
