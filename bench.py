@@ -228,6 +228,11 @@ def bench_ours(args):
         plans[mode] = srp.Plan(mic, grid, w["fs"], 343.0, w["K"], mode=mode, n_aux=w["n_aux"],
                                max_frames=L, host_io=(mode == "nyquist"))
         srp.srp_set_timing(plans[mode].handle, True)
+    # the conventional map on the CUDA cores too (the plain GPU path)
+    plans["conventional_cuda_cores"] = srp.Plan(mic, grid, w["fs"], 343.0, w["K"],
+                                                mode="conventional", max_frames=L,
+                                                engine="cuda_cores")
+    srp.srp_set_timing(plans["conventional_cuda_cores"].handle, True)
     ny = plans["nyquist"]
     Q, S = ny.info.Q, ny.info.S
 
@@ -243,10 +248,13 @@ def bench_ours(args):
     with ClockSampler(local) as clk:
         for mode, plan in plans.items():
             steps = args.steps if mode == "nyquist" else max(3, min(args.steps, args.conv_steps))
+            if mode == "conventional_cuda_cores":
+                steps = 3
             ms, st, wall = time_steps(make_step(plan), steps, args.warmup, flush, stream, world,
                                       stage_time(plan))
             launches = srp.srp_last_launch_count(plan.handle) * steps
-            res[mode] = dict(ms=ms, stage=st, wall=wall, steps=steps, launches=launches)
+            res[mode] = dict(ms=ms, stage=st, wall=wall, steps=steps, launches=launches,
+                             stages=srp.srp_stage_times(plan.handle))
     clocks = clk.summary()
 
     # map error of the Nyquist approximation w.r.t. conventional on one batch
@@ -276,6 +284,8 @@ def bench_ours(args):
     cells = J * Q * L
     ny_ms = reduce_max(res["nyquist"]["ms"].mean(), world, dev if world > 1 else None)
     cv_ms = reduce_max(res["conventional"]["ms"].mean(), world, dev if world > 1 else None)
+    cc_ms = reduce_max(res["conventional_cuda_cores"]["ms"].mean(), world,
+                       dev if world > 1 else None)
     k3_ms = float(np.mean(res["nyquist"]["stage"]))
     flops = 2.0 * J * S * L  # multiply-adds of the interpolation contraction, C_int x L
     achieved = flops / (k3_ms * 1e-3) / 1e12
@@ -298,6 +308,15 @@ def bench_ours(args):
                           / bf16_peak}
         pl.close()
 
+    conv_tc = bool(plans["conventional"].info.tensor_cores)
+    conv_stages = srp.srp_stage_times(plans["conventional"].handle)
+    for pl in plans.values():
+        pl.close()
+    extra = {}
+    if world == 1 and not args.no_batch:
+        extra["batched"] = bench_batched(args, flush, stream)
+    if world == 1 and not args.no_serve:
+        extra["serving"] = bench_serving(args)
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline(mic, grid, Ys[0], w, Q, S)
@@ -315,11 +334,17 @@ def bench_ours(args):
             "p50_ms": float(np.percentile(res["conventional"]["ms"], 50)),
             "p99_ms": float(np.percentile(res["conventional"]["ms"], 99)),
             "map_ms": float(np.mean(res["conventional"]["stage"])),
+            "engine": "tensor cores" if conv_tc else "CUDA cores",
+            "cuda_cores": {"value": world * cells / (cc_ms * 1e-3), "ms_per_step": cc_ms,
+                           "steps": 3,
+                           "map_ms": float(np.mean(res["conventional_cuda_cores"]["stage"]))},
         },
         "speedup_nyquist_over_conventional": cv_ms / ny_ms,
+        "speedup_nyquist_over_conventional_cuda_cores": cc_ms / ny_ms,
         "e_appr_db": {"median": float(np.median(e_appr)), "max": float(np.max(e_appr))},
         "map_error_bound": "FP32 path: max |map - FP64 oracle| <= 1e-4 x peak (tests)",
-        "stage_ms": {k: v for k, v in srp.srp_stage_times(plans["conventional"].handle).items()},
+        "stage_ms": res["nyquist"]["stages"],
+        "stage_ms_conventional": conv_stages,
         "roofline": {
             "kernel": "k_interp_tc<split> (on-chip sinc weights + tcgen05 MMA, FP32 as 3 BF16 products)",
             "bound": "tensor", "achieved": achieved, "peak": split_peak, "unit": "TFLOP/s",
@@ -339,7 +364,173 @@ def bench_ours(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    line.update(extra)
     print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+# batched uneven instances and serving
+# --------------------------------------------------------------------------
+
+BATCH_N, BATCH_L = 256, 32
+SERVE_STREAMS, SERVE_BLOCK, SERVE_RATE = 64, 8, 20000.0
+
+
+def mix_inputs(n, seed):
+    """n arrays of the uneven mix: M in 4..16, aperture 0.1-1 m, K in
+    {512, 1024, 2048}, 2D/3D grids with J log-uniform in [10k, 500k], L = 32."""
+    from paper_2012_09499_gb300 import synth
+    return [synth.uneven_instance(seed + i, L=BATCH_L) for i in range(n)]
+
+
+def bench_batched(args, flush, stream):
+    """The uneven mix in one graph launch per step (srp_map_batch), FP32 and
+    BF16, tiles chosen by the autotuner; L2 flushed between timed steps."""
+    import torch
+
+    from paper_2012_09499_gb300 import srp
+    cfgs = mix_inputs(BATCH_N, 1_000_000)
+    d_in = [torch.from_numpy(c["Y"]).cuda() for c in cfgs]
+    Js = np.array([c["grid"].shape[0] for c in cfgs], np.float64)
+    Ms = np.array([c["mic"].shape[0] for c in cfgs])
+    Qs = Ms * (Ms - 1) // 2
+    cells = float((Js * Qs).sum() * BATCH_L)
+    bf16_peak, peak_src = measured_bf16_peak()
+    out = {"workload": (f"{BATCH_N} arrays: M uniform in 4..16 mics in a cube of edge uniform in "
+                        f"0.1-1.0 m at the centre of a 6x7x3.5 m room, K in {{512,1024,2048}} at "
+                        f"16 kHz, 2D/3D cell-centre grids with J log-uniform in [10k, 500k] "
+                        f"(sum J = {int(Js.sum())}), L = {BATCH_L} frames each, N_aux = 2, "
+                        f"white sources at SNR 0-30 dB; one graph launch per step"),
+           "arrays": BATCH_N, "frames_per_array": BATCH_L, "sum_J": int(Js.sum()),
+           "mean_pairs": float(Qs.mean()), "l2": "flushed between timed steps (256 MB write)"}
+    L = [BATCH_L] * BATCH_N
+    for prec in ("fp32", "bf16"):
+        plans = [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], mode="nyquist", n_aux=2,
+                          precision=prec, max_frames=BATCH_L) for c in cfgs]
+        S = np.array([p.info.S for p in plans], np.float64)
+        flops = float((2.0 * Js * S * BATCH_L).sum())
+        batch = srp.Batch(plans)
+        outs = batch.outputs(L, "cuda")
+        maps, ams, pks = [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs]
+        srp.srp_batch_tune(batch.handle, d_in, L, maps, ams, pks)
+
+        def step(k):
+            srp.srp_map_batch(batch.handle, d_in, L, maps, ams, pks, stream)
+
+        steps = max(3, min(args.steps, args.batch_steps))
+        ms, _, _ = time_steps(step, steps, args.warmup, flush, stream, 1)
+        srp.srp_batch_set_timing(batch.handle, True)
+        st = []
+        for k in range(3):
+            flush(k)
+            step(k)
+            st.append(srp.srp_batch_stage_times(batch.handle))
+        srp.srp_batch_set_timing(batch.handle, False)
+        torch.cuda.synchronize()
+        srp.srp_batch_poll_device_status(batch.handle)
+        stage = {key: float(np.mean([x[key] for x in st])) for key in st[0]}
+        info = batch.info
+        peak = bf16_peak / 3.0 if prec == "fp32" else bf16_peak
+        achieved = flops / (stage["map"] * 1e-3) / 1e12
+        out[prec] = {
+            "value": cells / (float(ms.mean()) * 1e-3), "unit": UNIT,
+            "ms_per_step": float(ms.mean()), "steps": steps,
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "stage_ms": stage, "gpu_launches_per_step": int(info.launches),
+            "tiles": {"frames_per_item": info.tiles.frames_per_tile,
+                      "stages": info.tiles.stages, "ctas_per_sm": info.tiles.ctas_per_sm,
+                      "tuned_ms": float(info.tuned_ms)},
+            "work_items": int(info.items), "persistent_ctas": int(info.ctas),
+            "roofline": {"kernel": "k_map_batch_tc (persistent, on-chip sinc weights)",
+                         "bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "algorithmic": f"sum 2*J*S*L = {flops:.4g} flop per launch",
+                         "peak_source": f"measured bf16 {bf16_peak:.1f} TFLOP/s ({peak_src})"
+                                        + (" / 3 products" if prec == "fp32" else "")},
+        }
+        batch.close()
+        for p in plans:
+            p.close()
+        del outs, maps
+        torch.cuda.empty_cache()
+    return out
+
+
+def serve_run(srp, plans, cfgs, rate, duration, seed):
+    """Open-loop Poisson arrivals of SERVE_BLOCK-frame blocks from uniformly
+    chosen streams at `rate` frames/s for `duration` s; returns latencies
+    (ms, from each block's scheduled arrival) and throughput figures."""
+    import threading
+    srv = srp.Server(plans, device_budget_bytes=8 << 30, host_budget_bytes=2 << 30,
+                     max_inflight=2)
+    rng = np.random.default_rng(seed)
+    n_req = int(rate / SERVE_BLOCK * duration)
+    gaps = rng.exponential(SERVE_BLOCK / rate, n_req)
+    sched = np.cumsum(gaps)
+    who = rng.integers(0, len(plans), n_req)
+    blocks = rng.integers(0, BATCH_L // SERVE_BLOCK, n_req)
+    lag = {}
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k in range(n_req):
+            while True:
+                now = time.perf_counter() - t0
+                if now >= sched[k]:
+                    break
+                time.sleep(min(0.0005, sched[k] - now))
+            s, b = int(who[k]), int(blocks[k])
+            rid = srv.submit(s, cfgs[s]["Y"][b * SERVE_BLOCK:(b + 1) * SERVE_BLOCK], tag=k)
+            lag[rid] = time.perf_counter() - t0 - sched[k]
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    done = []
+    while th.is_alive():
+        done += srv.poll(wait_ms=20)
+    th.join()
+    done += srv.drain(timeout_s=120.0)
+    t_end = time.perf_counter() - t0
+    st = srv.stats
+    srv.close()
+    ok = [d for d in done if d["status"] == 0]
+    lat = np.array([d["t_done"] - d["t_submit"] + 1e3 * max(0.0, lag[d["id"]]) for d in ok])
+    frames = sum(d["L"] for d in ok)
+    cp = sum(d["L"] * plans[d["stream"]].info.J * plans[d["stream"]].info.Q for d in ok)
+    return {"requests": len(done), "completed": len(ok), "frames": frames,
+            "maps_per_s": frames / t_end, "cells_pairs_per_s": cp / t_end,
+            "offered_frames_per_s": rate, "wall_s": t_end,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "iterations": int(st.iterations),
+            "mean_frames_per_iteration": frames / max(1, int(st.iterations)),
+            "kernel_launches": int(st.kernel_launches),
+            "device_bytes_peak": int(st.device_bytes_peak),
+            "admission_waits": int(st.admission_waits),
+            "submit_lag_p99_ms": float(np.percentile([1e3 * v for v in lag.values()], 99))}
+
+
+def bench_serving(args):
+    """64 streams of the uneven mix, 8-frame blocks arriving as a Poisson
+    process at 20k frames/s in total: BF16 Nyquist, and the FP32
+    conventional map beside it at the same offered load for a shorter time."""
+    from paper_2012_09499_gb300 import srp
+    cfgs = mix_inputs(SERVE_STREAMS, 2_000_000)
+    out = {"streams": SERVE_STREAMS, "block_frames": SERVE_BLOCK,
+           "offered_frames_per_s": SERVE_RATE,
+           "arrivals": "Poisson (open loop), stream uniform, latency from scheduled arrival",
+           "device_budget_bytes": 8 << 30, "max_inflight": 2}
+    for name, mode, prec, dur in (("nyquist_bf16", "nyquist", "bf16", args.serve_seconds),
+                                  ("conventional_fp32", "conventional", "fp32",
+                                   min(args.serve_seconds, 1.0))):
+        plans = [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], mode=mode, n_aux=2,
+                          precision=prec, max_frames=BATCH_L) for c in cfgs]
+        res = serve_run(srp, plans, cfgs, SERVE_RATE, dur, 5)
+        res["duration_s"] = dur
+        res["tensor_core_streams"] = int(sum(p.info.tensor_cores for p in plans))
+        out[name] = res
+        for p in plans:
+            p.close()
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -414,6 +605,10 @@ def main(argv=None):
     ap.add_argument("--conv-steps", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
