@@ -255,6 +255,9 @@ typedef struct {
                                 at most 64 */
     int32_t stages;          /* operand pipeline depth in [2, 4]; 0 = the most that fit */
     int32_t ctas_per_sm;     /* persistent CTAs per SM, 1 or 2; 0 = 2 where they fit */
+    int32_t operand_a;       /* where the generated operand A lives: 1 = tensor memory
+                                (the MMAs read only B from shared memory), 2 = shared
+                                memory; 0 = tensor memory where it fits */
 } srp_batch_tiles;
 
 typedef struct {
@@ -288,8 +291,9 @@ SRP_API srp_status srp_map_batch(srp_batch b, const void *const *d_in, const int
 
 /* Autotuner: runs the call above with every tile shape that fits (frames per
  * item 16, 32, 64, 128 up to the largest L[i]; 2-4 stages; 1 or 2 CTAs per
- * SM), times each by CUDA events on s, keeps the fastest and leaves the
- * outputs of a final run with it.  Blocking.                              */
+ * SM; operand A in tensor or shared memory), times each by CUDA events on
+ * s, keeps the fastest and leaves the outputs of a final run with it.
+ * Blocking.                                                               */
 SRP_API srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const int32_t *L,
                                   float *const *d_maps, int32_t *const *d_argmax,
                                   float *const *d_peak, srp_stream_t s);

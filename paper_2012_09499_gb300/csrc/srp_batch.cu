@@ -83,6 +83,7 @@ struct PersistArgs {
     const int32_t *__restrict__ cta_first;  // [gridDim.x + 1]
     int N, stages;
     uint32_t idesc, tmem_cols;
+    uint32_t a_col0;        // operand A in TMEM: first column of the A stages
     int *status;
 };
 
@@ -229,7 +230,9 @@ __device__ __forceinline__ void sync_128() { asm volatile("bar.sync 1, 128;" :::
 // issue the MMAs by 16-slot step parity into two accumulators.  TMEM holds
 // two such accumulator pairs (item parity), columns [b 2N, b 2N + 2N).
 // ---------------------------------------------------------------------------
-template <bool kSplit, bool kHalf, bool kConv>
+// kTm: operand A is generated into TMEM after the accumulators (32 columns per
+// stage and part) and the MMAs read only B from shared memory.
+template <bool kSplit, bool kHalf, bool kConv, bool kTm>
 __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_constant__ CUtensorMap tmap,
                                                               const PersistArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + 132);
     const int N = a.N;
     const uint32_t b_tile = (uint32_t)N * 128u;
-    const uint32_t stage_bytes = (kSplit ? 2u : 1u) * (kATile + b_tile);
+    const uint32_t stage_bytes = (kSplit ? 2u : 1u) * ((kTm ? 0u : kATile) + b_tile);
     const uint32_t stage0 = base + 1024u;
     const uint32_t xring = stage0 + stage_bytes * (uint32_t)a.stages;
     float *mt = reinterpret_cast<float *>(gbase + 1024u + stage_bytes * (uint32_t)a.stages +
@@ -255,8 +258,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
     const uint32_t drain = smem_u32(&bars[12]);
     auto a_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes; };
     auto a_lo = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + kATile; };
-    auto b_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + (kSplit ? 2u : 1u) * kATile; };
+    auto b_hi = [&](int s) {
+        return stage0 + (uint32_t)s * stage_bytes + (kTm ? 0u : (kSplit ? 2u : 1u) * kATile);
+    };
     auto b_lo = [&](int s) { return b_hi(s) + b_tile; };
+    auto a_tm = [&](int s, int part) {
+        return a.a_col0 + ((uint32_t)s * (kSplit ? 2u : 1u) + (uint32_t)part) * 32u;
+    };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int it0 = a.cta_first[blockIdx.x], it1 = a.cta_first[blockIdx.x + 1];
@@ -434,7 +442,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                     read_next();
                 }
                 if (g >= a.stages) mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status);
-                const uint32_t a_row = a_hi(st) + row;
+                const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+                const uint32_t d0 = kTm ? tmem + lane_base + a_tm(st, 0) : a_hi(st) + row;
+                const uint32_t d1 = kTm ? tmem + lane_base + a_tm(st, 1) : 0u;
                 const int ng = cur.z;
                 if (kConv) {
                     const int k0 = cur.y;
@@ -442,21 +452,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                     float sn, cs;
                     sincospif(fmaf((float)rk, two_k, (float)k0 * f * two_k), &sn, &cs);
                     switch (ng) {
-                        case 2: gen_steer<2, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
-                        case 4: gen_steer<4, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
-                        case 6: gen_steer<6, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
-                        default: gen_steer<8, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
+                        case 2: gen_steer<2, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
+                        case 4: gen_steer<4, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
+                        case 6: gen_steer<6, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
+                        default: gen_steer<8, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
                     }
                 } else {
                     const float mc = x0f + __int_as_float(cur.y);
                     switch (ng) {
-                        case 2: gen_groups<2, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                        case 4: gen_groups<4, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                        case 6: gen_groups<6, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                        default: gen_groups<8, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                        case 2: gen_groups<2, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
+                        case 4: gen_groups<4, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
+                        case 6: gen_groups<6, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
+                        default: gen_groups<8, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
                     }
                 }
-                fence_proxy_async();
+                if (kTm) {  // TMEM stores complete and ordered before the MMA's reads
+                    tmem_wait_st();
+                    tc_fence_before();
+                } else {  // generic-proxy smem writes visible to the tensor core
+                    fence_proxy_async();
+                }
                 mbar_arrive(full_bar(st));
                 cur = nxt;
             }
@@ -535,15 +550,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                     tc_fence_after();
                     const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
                     const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
+                    const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
                     const int nk = __ldg(&ctab[c]).w;
                     for (int kk = par; kk < nk; kk += 2) {
                         const uint64_t adv = (uint64_t)(kk * 2);
-                        mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
-                        acc = 1;
-                        if (kSplit) {
-                            mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
-                            mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
+                        const uint32_t ac = (uint32_t)(kk * 8);
+                        if (kTm) {
+                            mma_f16_ts(dt, tah + ac, dbh + adv, a.idesc, acc);
+                            if (kSplit) {
+                                mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
+                                mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
+                            }
+                        } else {
+                            mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
+                            if (kSplit) {
+                                mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
+                                mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
+                            }
                         }
+                        acc = 1;
                     }
                     mma_commit(empty_bar(st));
                 }
@@ -575,25 +600,29 @@ namespace {
 
 struct TileChoice {
     int N = 0, stages = 0, cps = 0;
+    bool tm = false;  // operand A in TMEM
 };
 
 // Bytes of shared memory of the persistent kernel for a tile choice.
-size_t persist_smem(int N, int stages, bool split) {
-    const size_t stage = (split ? 2 : 1) * ((size_t)kATile + (size_t)N * 128);
-    return 2048 + stage * stages + (size_t)kXRing * 128 * 8 + (size_t)N * kMtStride * 4;
+size_t persist_smem(const TileChoice &t, bool split) {
+    const size_t stage = (split ? 2 : 1) * ((t.tm ? 0 : (size_t)kATile) + (size_t)t.N * 128);
+    return 2048 + stage * t.stages + (size_t)kXRing * 128 * 8 + (size_t)t.N * kMtStride * 4;
 }
 
-uint32_t persist_tmem_cols(int N) {
+// TMEM columns: two accumulator pairs (4N) and, with A in TMEM, 32 per stage
+// and part; rounded up to a power of two (the allocation unit).
+uint32_t persist_tmem_cols(const TileChoice &t, bool split) {
+    const uint32_t need = (uint32_t)(4 * t.N) + (t.tm ? (uint32_t)(t.stages * (split ? 2 : 1) * 32) : 0u);
     uint32_t cols = 32;
-    while (cols < (uint32_t)(4 * N)) cols <<= 1;
+    while (cols < need) cols <<= 1;
     return cols;
 }
 
 bool tile_fits(const TileChoice &t, bool split) {
     if (t.N < 16 || t.N > 256 || (t.N & 15)) return false;
     if (t.stages < 2 || t.stages > 4 || t.cps < 1 || t.cps > 2) return false;
-    if (persist_tmem_cols(t.N) * (uint32_t)t.cps > 512u) return false;
-    const size_t smem = persist_smem(t.N, t.stages, split);
+    if (persist_tmem_cols(t, split) * (uint32_t)t.cps > 512u) return false;
+    const size_t smem = persist_smem(t, split);
     if (smem > (size_t)kMaxSmemCta) return false;
     return (smem + 1024) * (size_t)t.cps <= (size_t)kSmemPerSm;
 }
@@ -784,18 +813,27 @@ srp_status batch_configure(srp_batch_s *b, const TileChoice &t) {
     pa.stages = t.stages;
     const uint32_t ab = b->half ? 0u : 1u;
     pa.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(t.N >> 3) << 17) | ((128u >> 4) << 24);
-    pa.tmem_cols = persist_tmem_cols(t.N);
+    pa.tmem_cols = persist_tmem_cols(t, b->split);
+    pa.a_col0 = (uint32_t)(4 * t.N);
     pa.status = b->d_status;
     // shared memory at launch: at least enough that no more than cps CTAs fit
     // on one SM (so that their TMEM columns always fit, 512 per SM)
-    size_t smem = persist_smem(t.N, t.stages, b->split);
+    size_t smem = persist_smem(t, b->split);
     smem = std::max(smem, ((size_t)kSmemPerSm / (t.cps + 1) - 1024 + 16 + 15) / 16 * 16);
     const bool conv = b->mode == SRP_MODE_CONV;
     void (*persist)(const CUtensorMap, const PersistArgs) =
-        conv ? (b->split ? k_map_batch_tc<true, false, true>
-                         : (b->half ? k_map_batch_tc<false, true, true> : k_map_batch_tc<false, false, true>))
-             : (b->split ? k_map_batch_tc<true, false, false>
-                         : (b->half ? k_map_batch_tc<false, true, false> : k_map_batch_tc<false, false, false>));
+        t.tm ? (conv ? (b->split ? k_map_batch_tc<true, false, true, true>
+                                 : (b->half ? k_map_batch_tc<false, true, true, true>
+                                            : k_map_batch_tc<false, false, true, true>))
+                     : (b->split ? k_map_batch_tc<true, false, false, true>
+                                 : (b->half ? k_map_batch_tc<false, true, false, true>
+                                            : k_map_batch_tc<false, false, false, true>)))
+             : (conv ? (b->split ? k_map_batch_tc<true, false, true, false>
+                                 : (b->half ? k_map_batch_tc<false, true, true, false>
+                                            : k_map_batch_tc<false, false, true, false>))
+                     : (b->split ? k_map_batch_tc<true, false, false, false>
+                                 : (b->half ? k_map_batch_tc<false, true, false, false>
+                                            : k_map_batch_tc<false, false, false, false>)));
     const int fmt = b->split ? 1 : (b->half ? 2 : 0);
     void (*operands)(const BatchInst *, const BatchCall *, int, uint16_t *) =
         conv ? (fmt == 0 ? k_batch_operands<0, true> : (fmt == 1 ? k_batch_operands<1, true> : k_batch_operands<2, true>))
@@ -967,15 +1005,21 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
     else t.N = std::min(64, round_up_int(b->max_L, 16));
     const bool given_stages = tiles != nullptr && tiles->stages != 0;
     const bool given_cps = tiles != nullptr && tiles->ctas_per_sm != 0;
+    const int given_a = tiles != nullptr ? tiles->operand_a : 0;
+    if (given_a < 0 || given_a > 2) return bail(fail(SRP_ERR_INVALID_ARG, "operand_a must be 0, 1 or 2"));
     TileChoice best;
-    for (int cps = 2; cps >= 1; --cps) {
-        if (given_cps && cps != tiles->ctas_per_sm) continue;
-        for (int st = 4; st >= 2; --st) {
-            if (given_stages && st != tiles->stages) continue;
-            TileChoice c = t;
-            c.cps = cps;
-            c.stages = st;
-            if (tile_fits(c, b->split) && best.N == 0) best = c;
+    for (int tm = 1; tm >= 0; --tm) {  // A in TMEM first
+        if ((given_a == 1 && !tm) || (given_a == 2 && tm)) continue;
+        for (int cps = 2; cps >= 1; --cps) {
+            if (given_cps && cps != tiles->ctas_per_sm) continue;
+            for (int st = 4; st >= 2; --st) {
+                if (given_stages && st != tiles->stages) continue;
+                TileChoice c = t;
+                c.cps = cps;
+                c.stages = st;
+                c.tm = tm != 0;
+                if (tile_fits(c, b->split) && best.N == 0) best = c;
+            }
         }
     }
     if (best.N == 0) return bail(fail(SRP_ERR_INVALID_ARG, "tile choice does not fit the SM"));
@@ -1023,12 +1067,14 @@ srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const int32_t *L
     srp_status result = SRP_OK;
     for (int N : Ns) {
         if (result != SRP_OK) break;
+        for (int tm = 0; tm <= 1 && result == SRP_OK; ++tm)
         for (int cps = 1; cps <= 2 && result == SRP_OK; ++cps)
             for (int stg = 2; stg <= 4 && result == SRP_OK; ++stg) {
                 TileChoice c;
                 c.N = N;
                 c.stages = stg;
                 c.cps = cps;
+                c.tm = tm != 0;
                 if (!tile_fits(c, b->split)) continue;
                 if ((result = batch_configure(b, c)) != SRP_OK) break;
                 float ms = 0.0f;
@@ -1069,6 +1115,7 @@ srp_status srp_batch_get_info(srp_batch b, srp_batch_info *info) {
     info->tiles.frames_per_tile = b->tiles.N;
     info->tiles.stages = b->tiles.stages;
     info->tiles.ctas_per_sm = b->tiles.cps;
+    info->tiles.operand_a = b->tiles.tm ? 1 : 2;
     info->launches = 3;
     info->tuned = b->tuned;
     info->tuned_ms = b->tuned_ms;

@@ -39,6 +39,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "srp_device.cuh"
 #include "srp_internal.h"
 #include "srp_tc_common.cuh"
@@ -131,11 +133,15 @@ struct TcArgs {
     int n_tiles;
     int *status;
     int vec_maps;           // maps rows are 8-byte aligned (float2 stores)
+    uint32_t a_col0;        // operand A in TMEM: first column of the A stages
     int par1_used;          // some chunk has two or more 16-lag steps
 };
 
 
-template <bool kSplit, bool kHalf, bool kConv>
+// kTm: operand A is generated into TMEM (32 columns per 64-slot stage and
+// part) and the MMAs read only B from shared memory; otherwise A is a
+// 128-byte-swizzled shared-memory tile like B.
+template <bool kSplit, bool kHalf, bool kConv, bool kTm>
 __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
                                                            const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -147,11 +153,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + 80);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + 84);
     const uint32_t b_tile = (uint32_t)a.N * 128u;
-    const uint32_t stage_bytes = (kSplit ? 2u : 1u) * (kATile + b_tile);
+    const uint32_t stage_bytes = (kSplit ? 2u : 1u) * ((kTm ? 0u : kATile) + b_tile);
     const uint32_t stage0 = base + 1024u;
-    // per-row ring of prefetched (TDOA, sp): xring[slot][row], 8 bytes each
-    const uint32_t xring = base + 1024u + stage_bytes * (uint32_t)a.stages;
-    // epilogue tile mt[frame][kMtStride] over the (then idle) stage buffers
+    // epilogue tile mt[frame][kMtStride] over the (then idle) stage buffers,
+    // then the per-row ring of prefetched (TDOA, sp): xring[slot][row], 8 bytes each
+    const uint32_t tile_bytes = ((uint32_t)a.N * (uint32_t)kMtStride * 4u + 1023u) & ~1023u;
+    const uint32_t xring = base + 1024u + max(stage_bytes * (uint32_t)a.stages, tile_bytes);
     float *mt = reinterpret_cast<float *>(gbase + 1024u);
 
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
@@ -159,7 +166,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
     const uint32_t accum_bar = smem_u32(&bars[8]);
     auto a_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes; };
     auto a_lo = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + kATile; };
-    auto b_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + (kSplit ? 2u : 1u) * kATile; };
+    auto b_hi = [&](int s) {
+        return stage0 + (uint32_t)s * stage_bytes + (kTm ? 0u : (kSplit ? 2u : 1u) * kATile);
+    };
+    // operand A of stage s in TMEM: part 0 (hi) then part 1 (lo), 32 columns each
+    auto a_tm = [&](int s, int part) {
+        return a.a_col0 + ((uint32_t)s * (kSplit ? 2u : 1u) + (uint32_t)part) * 32u;
+    };
     auto b_lo = [&](int s) { return b_hi(s) + b_tile; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -242,7 +255,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             const int ng = cur.z;
             if (c >= a.stages) mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status);
             // up to 64 weights, fully unrolled per group count
-            const uint32_t a_row = a_hi(st) + row;
+            const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+            const uint32_t d0 = kTm ? tmem + lane_base + a_tm(st, 0) : a_hi(st) + row;
+            const uint32_t d1 = kTm ? tmem + lane_base + a_tm(st, 1) : 0u;
             if (kConv) {
                 // exact seed e^{-j theta_k0} for the chunk's first bin k0 = cur.y
                 const int k0 = cur.y;
@@ -250,20 +265,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                 float sn, cs;
                 sincospif(fmaf((float)rk, two_k, (float)k0 * f * two_k), &sn, &cs);
                 switch (ng) {
-                    case 2: gen_steer<2, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
-                    case 4: gen_steer<4, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
-                    case 6: gen_steer<6, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
-                    default: gen_steer<8, kSplit, kHalf>(a_row, sw, cs, -sn, wp, wq); break;
+                    case 2: gen_steer<2, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
+                    case 4: gen_steer<4, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
+                    case 6: gen_steer<6, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
+                    default: gen_steer<8, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
                 }
             } else {
                 switch (ng) {
-                    case 2: gen_groups<2, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                    case 4: gen_groups<4, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                    case 6: gen_groups<6, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
-                    default: gen_groups<8, kSplit, kHalf>(a_row, sw, f, mc, sp); break;
+                    case 2: gen_groups<2, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
+                    case 4: gen_groups<4, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
+                    case 6: gen_groups<6, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
+                    default: gen_groups<8, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
                 }
             }
-            fence_proxy_async();
+            if (kTm) {  // TMEM stores complete and ordered before the MMA's reads
+                tmem_wait_st();
+                tc_fence_before();
+            } else {  // generic-proxy smem writes visible to the tensor core
+                fence_proxy_async();
+            }
             mbar_arrive(full_bar(st));
             cur = nxt;
         }
@@ -375,15 +395,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                 tc_fence_after();
                 const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
                 const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
+                const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
                 const int nk = __ldg(&a.ctab[c]).w;  // 16-lag steps holding lags of the pair
                 for (int kk = par; kk < nk; kk += 2) {
                     const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
-                    mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
-                    acc = 1;
-                    if (kSplit) {
-                        mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
-                        mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
+                    const uint32_t ac = (uint32_t)(kk * 8);   // 16 values in 8 TMEM columns
+                    if (kTm) {
+                        mma_f16_ts(dt, tah + ac, dbh + adv, a.idesc, acc);
+                        if (kSplit) {
+                            mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
+                            mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
+                        }
+                    } else {
+                        mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
+                        if (kSplit) {
+                            mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
+                            mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
+                        }
                     }
+                    acc = 1;
                 }
                 mma_commit(empty_bar(st));
             }
@@ -422,19 +452,27 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-template <bool kSplit, bool kHalf, bool kConv>
+template <bool kSplit, bool kHalf, bool kConv, bool kTm>
 cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_t smem,
                       cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv>,
+        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv, kTm>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_interp_tc<kSplit, kHalf, kConv><<<dim3((unsigned)a.n_tiles, grid_y), kThreads, smem, s>>>(map, a);
+    k_interp_tc<kSplit, kHalf, kConv, kTm>
+        <<<dim3((unsigned)a.n_tiles, grid_y), kThreads, smem, s>>>(map, a);
     return cudaGetLastError();
+}
+
+template <bool kSplit, bool kHalf, bool kConv>
+cudaError_t launch_tc_a(const CUtensorMap &map, const TcArgs &a, bool tm, int grid_y, size_t smem,
+                        cudaStream_t s) {
+    return tm ? launch_tc<kSplit, kHalf, kConv, true>(map, a, grid_y, smem, s)
+              : launch_tc<kSplit, kHalf, kConv, false>(map, a, grid_y, smem, s);
 }
 
 }  // namespace
@@ -512,19 +550,38 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     // or FP16 (0), both K-major, N >> 3 at bit 17, M = 128 >> 4 at bit 24.
     const uint32_t ab = half ? 0u : 1u;
     a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
-    uint32_t cols = 32;
-    while (cols < (uint32_t)(2 * N)) cols <<= 1;  // two accumulators
-    a.tmem_cols = cols;
-    const size_t stage = (split ? 2 : 1) * (size_t)(kATile + (uint32_t)N * 128u);
+    const int hs = split ? 2 : 1;
     const size_t fixed = 1024 + 1024 + (size_t)kXRing * 128 * sizeof(int2);
-    const size_t tile_bytes = (size_t)N * kMtStride * sizeof(float);  // epilogue tile
-    // two stages (or more if they fit in half the SM) and at most four; the
-    // stages must also hold the epilogue tile
-    int stages = (int)((113 * 1024 - fixed) / stage);
-    if (stages < 2) stages = (int)((227 * 1024 - fixed) / stage);
-    if (stages > 4) stages = 4;
-    while (stages * stage < tile_bytes && fixed + (stages + 1) * stage <= 227 * 1024) ++stages;
-    if (stages < 2 || stages * stage < tile_bytes) return cudaErrorInvalidConfiguration;
+    const size_t tile_bytes = ((size_t)N * kMtStride * sizeof(float) + 1023) / 1024 * 1024;
+    // Operand A in TMEM when two CTAs per SM keep 2N accumulator columns and at
+    // least two A stages (32 columns per part) within 256 columns each.
+    const bool tm = 2 * N + 2 * hs * 32 <= 256;
+    int stages;
+    size_t smem;
+    if (tm) {
+        stages = 4;
+        while (2 * N + stages * hs * 32 > 256) --stages;
+        a.tmem_cols = 256;
+        a.a_col0 = (uint32_t)(2 * N);
+        const size_t stage = (size_t)hs * N * 128;
+        smem = fixed + std::max(stage * (size_t)stages, tile_bytes);
+        // at least 78 KB: no third CTA (whose TMEM allocation would wait) on an SM
+        smem = std::max(smem, (size_t)(78 * 1024));
+    } else {
+        uint32_t cols = 32;
+        while (cols < (uint32_t)(2 * N)) cols <<= 1;  // two accumulators
+        a.tmem_cols = cols;
+        a.a_col0 = 0;
+        const size_t stage = (size_t)hs * (kATile + (uint32_t)N * 128u);
+        // two stages (or more if they fit in half the SM) and at most four; the
+        // stages must also hold the epilogue tile
+        stages = (int)((113 * 1024 - fixed) / stage);
+        if (stages < 2) stages = (int)((227 * 1024 - fixed) / stage);
+        if (stages > 4) stages = 4;
+        while (stages * stage < tile_bytes && fixed + (stages + 1) * stage <= 227 * 1024) ++stages;
+        if (stages < 2 || stages * stage < tile_bytes) return cudaErrorInvalidConfiguration;
+        smem = fixed + stage * (size_t)stages;
+    }
     a.stages = stages;
     a.maps = maps;
     a.part = part;
@@ -533,17 +590,16 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.par1_used = par1_used;
     a.K = K;
     a.vec_maps = (maps != nullptr && (J % 2) == 0 && (reinterpret_cast<uintptr_t>(maps) & 7) == 0);
-    const size_t smem = fixed + stage * (size_t)stages;
     const int grid_y = (L + N - 1) / N;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(xi_map);
     if (conv) {
-        if (split) return launch_tc<true, false, true>(map, a, grid_y, smem, s);
-        if (half) return launch_tc<false, true, true>(map, a, grid_y, smem, s);
-        return launch_tc<false, false, true>(map, a, grid_y, smem, s);
+        if (split) return launch_tc_a<true, false, true>(map, a, tm, grid_y, smem, s);
+        if (half) return launch_tc_a<false, true, true>(map, a, tm, grid_y, smem, s);
+        return launch_tc_a<false, false, true>(map, a, tm, grid_y, smem, s);
     }
-    if (split) return launch_tc<true, false, false>(map, a, grid_y, smem, s);
-    if (half) return launch_tc<false, true, false>(map, a, grid_y, smem, s);
-    return launch_tc<false, false, false>(map, a, grid_y, smem, s);
+    if (split) return launch_tc_a<true, false, false>(map, a, tm, grid_y, smem, s);
+    if (half) return launch_tc_a<false, true, false>(map, a, tm, grid_y, smem, s);
+    return launch_tc_a<false, false, false>(map, a, tm, grid_y, smem, s);
 }
 
 }  // namespace srp

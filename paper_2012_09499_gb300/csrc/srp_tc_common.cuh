@@ -130,6 +130,29 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t 
         : "memory");
 }
 
+// D[tmem] (+)= A[tmem] * B[smem]^T, kind::f16: A's rows are TMEM lanes and each
+// 32-bit column holds two consecutive K elements (the lower K in the low half).
+__device__ __forceinline__ void mma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p; }" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Four consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c,
+                                         uint32_t d) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+                 "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -224,14 +247,32 @@ __device__ __forceinline__ uint32_t pack_f16(float a, float b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// Weights of NG groups of 8 lags for one candidate row of the A tile(s):
+// Store group cc of a candidate row of operand A: 8 16-bit values hv (and,
+// with kSplit, their low parts lv).  kTm: into TMEM, four 32-bit columns per
+// group from column dst0 (dst1 for the low parts) of this thread's lane.
+// Otherwise into the shared-memory A tile with the 128-byte swizzle: row
+// address dst0, 16-byte chunk (cc0 + cc) ^ sw, low parts kATile bytes on.
+template <bool kSplit, bool kTm>
+__device__ __forceinline__ void store_group(uint32_t dst0, uint32_t dst1, uint32_t sw,
+                                            uint32_t cc, const uint32_t (&hv)[4],
+                                            const uint32_t (&lv)[4]) {
+    if (kTm) {
+        tmem_st4(dst0 + 4u * cc, hv[0], hv[1], hv[2], hv[3]);
+        if (kSplit) tmem_st4(dst1 + 4u * cc, lv[0], lv[1], lv[2], lv[3]);
+    } else {
+        const uint32_t off = dst0 + ((cc ^ sw) << 4);
+        st_shared_v4(off, hv[0], hv[1], hv[2], hv[3]);
+        if (kSplit) st_shared_v4(off + kATile, lv[0], lv[1], lv[2], lv[3]);
+    }
+}
+
+// Weights of NG groups of 8 lags for one candidate row of operand A:
 // w = sp / d with d = f + (mc - k) for lag slot k of the chunk, two lags per
-// reciprocal, written at row offset a_row with the 128-byte swizzle (chunk
-// position cc ^ sw).  With kSplit, the low part bf16(w - hi) goes to the tile
-// kATile bytes further on.
-template <int NG, bool kSplit, bool kHalf>
-__device__ __forceinline__ void gen_groups(uint32_t a_row, uint32_t sw, float f, float mc,
-                                           float sp) {
+// reciprocal, stored by store_group (groups cc0 .. cc0 + NG - 1 of the row).
+// With kSplit, the low parts bf16(w - hi) are stored too.
+template <int NG, bool kSplit, bool kHalf, bool kTm>
+__device__ __forceinline__ void gen_groups(uint32_t dst0, uint32_t dst1, uint32_t sw, float f,
+                                           float mc, float sp, uint32_t cc0 = 0) {
     const uint64_t f2 = pk2(f, f);
     const uint64_t two = pk2(2.0f, 2.0f);
     // m2 = (mc - k - 1, mc - k): the second lag of a pair first, so that
@@ -239,7 +280,7 @@ __device__ __forceinline__ void gen_groups(uint32_t a_row, uint32_t sw, float f,
     uint64_t m2 = pk2(mc - 1.0f, mc);
 #pragma unroll
     for (int cc = 0; cc < NG; ++cc) {
-        uint32_t hv[4], lv[4];
+        uint32_t hv[4], lv[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const uint64_t d2 = add2(f2, m2);  // (db, da), each rounded once
@@ -259,24 +300,22 @@ __device__ __forceinline__ void gen_groups(uint32_t a_row, uint32_t sw, float f,
                 }
             }
         }
-        const uint32_t off = a_row + (((uint32_t)cc ^ sw) << 4);
-        st_shared_v4(off, hv[0], hv[1], hv[2], hv[3]);
-        if (kSplit) st_shared_v4(off + kATile, lv[0], lv[1], lv[2], lv[3]);
+        store_group<kSplit, kTm>(dst0, dst1, sw, (uint32_t)cc + cc0, hv, lv);
     }
 }
 
-// Steering weights of NG groups (4 bins each) for this thread's row: the
+// Steering weights of NG groups (4 bins each) for this thread's row of A: the
 // element pair (cos theta_k, -sin theta_k) of bins k0, k0 + 1, ..., i.e.
 // z = e^{-j theta_k}, starting from z0 and multiplied per bin by
 // w' = (p, q) = e^{-j 2 pi x / K}: z w' = (a p - b q, b p + a q) for z = (a, b).
-template <int NG, bool kSplit, bool kHalf>
-__device__ __forceinline__ void gen_steer(uint32_t a_row, uint32_t sw, float za, float zb,
-                                          float p, float q) {
+template <int NG, bool kSplit, bool kHalf, bool kTm>
+__device__ __forceinline__ void gen_steer(uint32_t dst0, uint32_t dst1, uint32_t sw, float za,
+                                          float zb, float p, float q, uint32_t cc0 = 0) {
     uint64_t z = pk2(za, zb);
     const uint64_t pp = pk2(p, p), qq = pk2(-q, q);
 #pragma unroll
     for (int cc = 0; cc < NG; ++cc) {
-        uint32_t hv[4], lv[4];
+        uint32_t hv[4], lv[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float2 v = upk2(z);
@@ -296,9 +335,7 @@ __device__ __forceinline__ void gen_steer(uint32_t a_row, uint32_t sw, float za,
                 }
             }
         }
-        const uint32_t off = a_row + (((uint32_t)cc ^ sw) << 4);
-        st_shared_v4(off, hv[0], hv[1], hv[2], hv[3]);
-        if (kSplit) st_shared_v4(off + kATile, lv[0], lv[1], lv[2], lv[3]);
+        store_group<kSplit, kTm>(dst0, dst1, sw, (uint32_t)cc + cc0, hv, lv);
     }
 }
 

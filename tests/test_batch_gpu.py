@@ -140,13 +140,19 @@ def test_batch_tuner_and_explicit_tiles():
     for (m, a, p), ref in zip(run_batch(batch, cfgs, L), refs):
         check(m, a, p, ref, TOL["fp32"])
     batch.close()
-    # a fixed tile shape: 16 frames per item, two stages, one CTA per SM
-    b2 = srp.Batch(plans, tiles=(16, 2, 1))
-    assert (b2.info.tiles.frames_per_tile, b2.info.tiles.stages,
-            b2.info.tiles.ctas_per_sm) == (16, 2, 1)
-    for (m, a, p), ref in zip(run_batch(b2, cfgs, L), refs):
-        check(m, a, p, ref, TOL["fp32"])
-    b2.close()
+    # a fixed tile shape: 16 frames per item, two stages, one CTA per SM, with
+    # operand A in tensor memory (1) and in shared memory (2): same results
+    outs = {}
+    for where in (1, 2):
+        b2 = srp.Batch(plans, tiles=(16, 2, 1, where))
+        assert (b2.info.tiles.frames_per_tile, b2.info.tiles.stages,
+                b2.info.tiles.ctas_per_sm, b2.info.tiles.operand_a) == (16, 2, 1, where)
+        outs[where] = run_batch(b2, cfgs, L)
+        for (m, a, p), ref in zip(outs[where], refs):
+            check(m, a, p, ref, TOL["fp32"])
+        b2.close()
+    for (m1, a1, _), (m2, a2, _) in zip(outs[1], outs[2]):
+        assert np.array_equal(m1, m2) and np.array_equal(a1, a2)
 
 
 def test_batch_full_scale_sampled():
