@@ -37,7 +37,7 @@ WORKLOAD = dict(name="room_3d", M=8, J=480000, K=1024, L=64, n_aux=2, fs=16000.0
 FLUSH_BYTES = 256 << 20
 # DRAM read + write bytes of one k_interp_tc<split> launch on this workload,
 # from ncu (profiles/k_interp_tc_room_3d.md); None once the kernel changes.
-K3_TRAFFIC_BYTES = 183.1e6
+K3_TRAFFIC_BYTES = None
 
 
 def config_dict(Q, S):
@@ -162,10 +162,11 @@ def make_batches(rank: int, n: int):
     return mic, grid, Ys
 
 
-def time_steps(step, steps, warmup, flush, stream, world, timed_stage=None):
+def time_steps(step, steps, warmup, flush, stream, world, timed_stage=None, name="timed"):
     """Runs warmup + steps; returns per-step device ms (CUDA events on the
     launching stream, L2 flushed before each step) and, if timed_stage is
-    given, per-step ms of that stage from the library's own events."""
+    given, per-step ms of that stage from the library's own events.  The
+    timed steps run inside the NVTX range `name` (for profiler filters)."""
     import torch
     for w in range(warmup):
         step(w)
@@ -175,6 +176,7 @@ def time_steps(step, steps, warmup, flush, stream, world, timed_stage=None):
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     stage_ms = []
+    torch.cuda.nvtx.range_push(name)
     t_wall = time.perf_counter()
     for k in range(steps):
         flush(k)
@@ -187,6 +189,7 @@ def time_steps(step, steps, warmup, flush, stream, world, timed_stage=None):
     barrier(world)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
+    torch.cuda.nvtx.range_pop()
     ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
     return ms, np.array(stage_ms), wall
 
@@ -251,7 +254,7 @@ def bench_ours(args):
             if mode == "conventional_cuda_cores":
                 steps = 3
             ms, st, wall = time_steps(make_step(plan), steps, args.warmup, flush, stream, world,
-                                      stage_time(plan))
+                                      stage_time(plan), name=f"room_3d_{mode}")
             launches = srp.srp_last_launch_count(plan.handle) * steps
             res[mode] = dict(ms=ms, stage=st, wall=wall, steps=steps, launches=launches,
                              stages=srp.srp_stage_times(plan.handle))
@@ -300,7 +303,7 @@ def bench_ours(args):
                       max_frames=L, precision=prec)
         srp.srp_set_timing(pl.handle, True)
         ms_v, st_v, _ = time_steps(make_step(pl), max(3, min(args.steps, 20)), args.warmup,
-                                   flush, stream, world, stage_time(pl))
+                                   flush, stream, world, stage_time(pl), name=f"room_3d_{prec}")
         variants[prec] = {"ms_per_step": float(ms_v.mean()),
                           "value": world * J * Q * L / (float(ms_v.mean()) * 1e-3),
                           "map_ms": float(st_v.mean()),
@@ -389,21 +392,22 @@ def bench_batched(args, flush, stream):
     import torch
 
     from paper_2012_09499_gb300 import srp
-    cfgs = mix_inputs(BATCH_N, 1_000_000)
+    n_arrays = args.batch_arrays
+    cfgs = mix_inputs(n_arrays, 1_000_000)
     d_in = [torch.from_numpy(c["Y"]).cuda() for c in cfgs]
     Js = np.array([c["grid"].shape[0] for c in cfgs], np.float64)
     Ms = np.array([c["mic"].shape[0] for c in cfgs])
     Qs = Ms * (Ms - 1) // 2
     cells = float((Js * Qs).sum() * BATCH_L)
     bf16_peak, peak_src = measured_bf16_peak()
-    out = {"workload": (f"{BATCH_N} arrays: M uniform in 4..16 mics in a cube of edge uniform in "
+    out = {"workload": (f"{n_arrays} arrays: M uniform in 4..16 mics in a cube of edge uniform in "
                         f"0.1-1.0 m at the centre of a 6x7x3.5 m room, K in {{512,1024,2048}} at "
                         f"16 kHz, 2D/3D cell-centre grids with J log-uniform in [10k, 500k] "
                         f"(sum J = {int(Js.sum())}), L = {BATCH_L} frames each, N_aux = 2, "
                         f"white sources at SNR 0-30 dB; one graph launch per step"),
-           "arrays": BATCH_N, "frames_per_array": BATCH_L, "sum_J": int(Js.sum()),
+           "arrays": n_arrays, "frames_per_array": BATCH_L, "sum_J": int(Js.sum()),
            "mean_pairs": float(Qs.mean()), "l2": "flushed between timed steps (256 MB write)"}
-    L = [BATCH_L] * BATCH_N
+    L = [BATCH_L] * n_arrays
     for prec in ("fp32", "bf16"):
         plans = [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], mode="nyquist", n_aux=2,
                           precision=prec, max_frames=BATCH_L) for c in cfgs]
@@ -418,7 +422,7 @@ def bench_batched(args, flush, stream):
             srp.srp_map_batch(batch.handle, d_in, L, maps, ams, pks, stream)
 
         steps = max(3, min(args.steps, args.batch_steps))
-        ms, _, _ = time_steps(step, steps, args.warmup, flush, stream, 1)
+        ms, _, _ = time_steps(step, steps, args.warmup, flush, stream, 1, name=f"batched_{prec}")
         srp.srp_batch_set_timing(batch.handle, True)
         st = []
         for k in range(3):
@@ -608,6 +612,8 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-arrays", type=int, default=BATCH_N,
+                    help="arrays of the uneven mix in the batched section (the workload is 256)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:

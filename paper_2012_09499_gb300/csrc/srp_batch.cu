@@ -45,7 +45,7 @@ namespace {
 using namespace dev;
 using namespace tc;
 
-constexpr int kPairBlock = 8;         // pairs per CTA of the operand kernel
+constexpr int kPairBlock = 4;         // pairs per CTA of the operand kernel
 constexpr int kMaxSmemCta = 227 * 1024;
 constexpr int kSmemPerSm = 228 * 1024;  // shared memory per SM (1 KB of it reserved per CTA)
 
@@ -126,57 +126,63 @@ __global__ void __launch_bounds__(128) k_batch_operands(const BatchInst *__restr
     const int K = I.K, Kb = K / 2 + 1, Q = I.Q;
     const int hs = kFmt == 1 ? 2 : 1;
     const float2 *in = static_cast<const float2 *>(call[p].in);
-    float2 *tw = sm, *ps = sm + K;
-    if (!kConv)
-        for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = I.twid[j];
-    const int q1 = min(Q, (pb + 1) * kPairBlock);
+    float2 *tw = sm, *ps = sm + K;  // Nyquist: twiddles, then kPairBlock spectrum rows
+    const int q0 = pb * kPairBlock, np = min(Q, q0 + kPairBlock) - q0;
     // slot s of frame l, part h, lives at row b_row0 + ((s >> 6) hs + h) Lb + l
     auto elem = [&](int s, int h) -> size_t {
         return (size_t)(I.b_row0 + (int64_t)((s >> 6) * hs + h) * I.Lb + l) * 64 + (s & 63);
     };
-    for (int q = pb * kPairBlock; q < q1; ++q) {
-        const int2 pr = I.pairs[q];
-        const int base = I.offc[q];
+    // cross spectrum of pair q0 + j, bin k
+    auto cross = [&](int j, int k) -> float2 {
+        const int q = q0 + j;
+        if (I.input_kind == SRP_IN_STFT) {
+            const int2 pr = I.pairs[q];
+            return phat_cross(unit_phase(in[((size_t)l * I.M + pr.x) * Kb + k]),
+                              unit_phase(in[((size_t)l * I.M + pr.y) * Kb + k]));
+        }
+        return in[((size_t)l * Q + q) * Kb + k];
+    };
+    if (kConv) {
+        for (int j = 0; j < np; ++j)
         for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
-            float2 v;
-            if (I.input_kind == SRP_IN_STFT)
-                v = phat_cross(unit_phase(in[((size_t)l * I.M + pr.x) * Kb + k]),
-                               unit_phase(in[((size_t)l * I.M + pr.y) * Kb + k]));
-            else
-                v = in[((size_t)l * Q + q) * Kb + k];
-            const float a = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
-            if (kConv) {
-                const float re = a / (float)K * v.x, im = a / (float)K * v.y;
-                const size_t e = elem(base + 2 * k, 0);
-                uint32_t h, lo = 0;
-                if (kFmt == 2) {
-                    h = pack_f16(re, im);
-                } else {
-                    h = pack_bf16(re, im);
-                    if (kFmt == 1)
-                        lo = pack_bf16(re - __uint_as_float(h << 16),
-                                       im - __uint_as_float(h & 0xFFFF0000u));
-                }
-                *reinterpret_cast<uint32_t *>(b16 + e) = h;
-                if (kFmt == 1) *reinterpret_cast<uint32_t *>(b16 + elem(base + 2 * k, 1)) = lo;
+            const float2 v = cross(j, k);
+            const float a = ((k == 0 || 2 * k == K) ? 1.0f : 2.0f) / (float)K;
+            const float re = a * v.x, im = a * v.y;
+            const int s = I.offc[q0 + j] + 2 * k;
+            uint32_t h, lo = 0;
+            if (kFmt == 2) {
+                h = pack_f16(re, im);
             } else {
-                ps[k] = make_float2(a * v.x, a * v.y);
+                h = pack_bf16(re, im);
+                if (kFmt == 1)
+                    lo = pack_bf16(re - __uint_as_float(h << 16),
+                                   im - __uint_as_float(h & 0xFFFF0000u));
             }
+            *reinterpret_cast<uint32_t *>(b16 + elem(s, 0)) = h;
+            if (kFmt == 1) *reinterpret_cast<uint32_t *>(b16 + elem(s, 1)) = lo;
         }
-        if (!kConv) {
-            __syncthreads();
-            gcc_row(tw, ps, K, I.nq[q] + I.n_aux, [&](int t, int nl, float v) {
-                if (nl & 1) v = -v;
-                const uint16_t h = to16(v, kFmt == 2);
-                b16[elem(base + t, 0)] = h;
-                if (kFmt == 1) {
-                    __nv_bfloat16 hb = *reinterpret_cast<const __nv_bfloat16 *>(&h);
-                    b16[elem(base + t, 1)] = to16(v - __bfloat162float(hb), 0);
-                }
-            });
-            __syncthreads();
-        }
+        return;
     }
+    // Nyquist: a_k psi of every pair of the block, then its critical samples
+    for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = I.twid[j];
+    for (int j = 0; j < np; ++j)
+        for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
+            const float2 v = cross(j, k);
+            const float a = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
+            ps[j * Kb + k] = make_float2(a * v.x, a * v.y);
+        }
+    __syncthreads();
+    gcc_rows(tw, ps, Kb, np, K, [&](int j) { return I.nq[q0 + j] + I.n_aux; },
+             [&](int j, int t, int nl, float v) {
+                 if (nl & 1) v = -v;
+                 const int s = I.offc[q0 + j] + t;
+                 const uint16_t h = to16(v, kFmt == 2);
+                 b16[elem(s, 0)] = h;
+                 if (kFmt == 1) {
+                     __nv_bfloat16 hb = *reinterpret_cast<const __nv_bfloat16 *>(&h);
+                     b16[elem(s, 1)] = to16(v - __bfloat162float(hb), 0);
+                 }
+             });
 }
 
 // ---------------------------------------------------------------------------
@@ -838,7 +844,8 @@ srp_status batch_configure(srp_batch_s *b, const TileChoice &t) {
     void (*operands)(const BatchInst *, const BatchCall *, int, uint16_t *) =
         conv ? (fmt == 0 ? k_batch_operands<0, true> : (fmt == 1 ? k_batch_operands<1, true> : k_batch_operands<2, true>))
              : (fmt == 0 ? k_batch_operands<0, false> : (fmt == 1 ? k_batch_operands<1, false> : k_batch_operands<2, false>));
-    const size_t op_smem = conv ? 0 : sizeof(float2) * (size_t)(b->max_K + b->max_K / 2 + 1);
+    const size_t op_smem =
+        conv ? 0 : sizeof(float2) * (size_t)(b->max_K + kPairBlock * (b->max_K / 2 + 1));
     SRP_CUDA(cudaFuncSetAttribute(persist, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemCta),
              "persistent kernel attribute");
     SRP_CUDA(cudaFuncSetAttribute(operands, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -969,7 +976,7 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         b->max_L = std::max(b->max_L, L.L_max);
         b->max_K = std::max(b->max_K, L.K);
     }
-    if (sizeof(float2) * (size_t)(b->max_K + b->max_K / 2 + 1) > (size_t)kMaxSmemCta)
+    if (sizeof(float2) * (size_t)(b->max_K + kPairBlock * (b->max_K / 2 + 1)) > (size_t)kMaxSmemCta)
         return bail(fail(SRP_ERR_UNSUPPORTED, "K too large for the batched operand kernel"));
     if ((e = cudaMalloc(&b->d_part, part)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     b->part_bytes = part;
