@@ -499,6 +499,8 @@ def serve_run(srp, plans, cfgs, rate, duration, seed):
     srv.close()
     ok = [d for d in done if d["status"] == 0]
     lat = np.array([d["t_done"] - d["t_submit"] + 1e3 * max(0.0, lag[d["id"]]) for d in ok])
+    wait = np.array([d["t_start"] - d["t_submit"] for d in ok])  # queued on the host
+    run = np.array([d["t_done"] - d["t_start"] for d in ok])     # its iteration, copies included
     frames = sum(d["L"] for d in ok)
     cp = sum(d["L"] * plans[d["stream"]].info.J * plans[d["stream"]].info.Q for d in ok)
     return {"requests": len(done), "completed": len(ok), "frames": frames,
@@ -506,6 +508,10 @@ def serve_run(srp, plans, cfgs, rate, duration, seed):
             "offered_frames_per_s": rate, "wall_s": t_end,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "iterations": int(st.iterations),
+            "queued_p50_ms": float(np.percentile(wait, 50)),
+            "queued_p99_ms": float(np.percentile(wait, 99)),
+            "iteration_p50_ms": float(np.percentile(run, 50)),
+            "iteration_p99_ms": float(np.percentile(run, 99)),
             "mean_frames_per_iteration": frames / max(1, int(st.iterations)),
             "kernel_launches": int(st.kernel_launches),
             "device_bytes_peak": int(st.device_bytes_peak),

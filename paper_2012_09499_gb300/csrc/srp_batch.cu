@@ -79,7 +79,8 @@ struct BatchCall {
 struct PersistArgs {
     const BatchInst *__restrict__ inst;
     const BatchCall *__restrict__ call;
-    const int4 *__restrict__ items;      // {plan, tile, l0, cost}, CTA lists back to back
+    const int4 *__restrict__ items;      // {plan, tile, l0, items left in the (plan, l0) run},
+                                         // CTA lists back to back
     const int32_t *__restrict__ cta_first;  // [gridDim.x + 1]
     int N, stages;
     uint32_t idesc, tmem_cols;
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
         int64_t ljp = 0;
         auto load_next = [&]() {
             if (lq == 0) {
-                while (li < it1 && !live(a.items[li])) ++li;
+                while (li < it1 && !live(a.items[li])) li += a.items[li].w;
                 if (li < it1) {
                     const int4 it = a.items[li];
                     const BatchInst &I = a.inst[it.x];
@@ -414,7 +415,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
         int4 prev = make_int4(-1, 0, 0, 0);
         for (int t = it0; t < it1; ++t) {
             const int4 it = a.items[t];
-            if (!live(it)) continue;
+            if (!live(it)) {  // skip the rest of this (plan, frame tile) run
+                t += it.w - 1;
+                continue;
+            }
             if (!and_128(*abort_flag == 0)) break;
             const BatchInst &I = a.inst[it.x];
             const int n_chunks = I.n_chunks, xf = I.xf;
@@ -495,7 +499,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
             bool ok = true;
             for (int t = it0; t < it1 && ok; ++t) {
                 const int4 it = a.items[t];
-                if (!live(it)) continue;
+                if (!live(it)) {
+                    t += it.w - 1;
+                    continue;
+                }
                 const BatchInst &I = a.inst[it.x];
                 const int n_chunks = I.n_chunks, Lb = I.Lb;
                 const int64_t r0 = I.b_row0 + it.z;
@@ -536,7 +543,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
             bool ok = true;
             for (int t = it0; t < it1 && ok; ++t) {
                 const int4 it = a.items[t];
-                if (!live(it)) continue;
+                if (!live(it)) {
+                    t += it.w - 1;
+                    continue;
+                }
                 const BatchInst &I = a.inst[it.x];
                 const int b = kx & 1;
                 if (!mbar_wait(acc_empty(b), ((uint32_t)(kx >> 1) & 1u) ^ 1u, abort_flag, a.status))
@@ -771,12 +781,22 @@ srp_status batch_configure(srp_batch_s *b, const TileChoice &t) {
     std::vector<int4> sched;
     sched.reserve(items.size());
     std::vector<int32_t> first(ctas + 1, 0);
+    // Within a CTA the items run grouped by (plan, frame tile), and .w holds
+    // the items left in the group: a call that skips a plan (or its later
+    // frames) skips the group with one test.
     for (int c = 0; c < ctas; ++c) {
         first[c] = (int32_t)sched.size();
-        for (int k : lists[c]) {
-            int4 it = items[k];
-            it.w = (int)cost[k];
-            sched.push_back(it);
+        std::vector<int> &lc = lists[c];
+        std::stable_sort(lc.begin(), lc.end(), [&](int x, int y) {
+            return items[x].x != items[y].x ? items[x].x < items[y].x : items[x].z < items[y].z;
+        });
+        for (size_t k = 0; k < lc.size(); ++k) sched.push_back(items[lc[k]]);
+        const size_t e = sched.size();
+        for (size_t k = first[c]; k < e;) {
+            size_t r = k;
+            while (r < e && sched[r].x == sched[k].x && sched[r].z == sched[k].z) ++r;
+            for (size_t j = k; j < r; ++j) sched[j].w = (int)(r - j);
+            k = r;
         }
     }
     first[ctas] = (int32_t)sched.size();
