@@ -107,7 +107,8 @@ typedef struct {
     srp_precision precision;  /* arithmetic of the map contraction */
     srp_input_kind input_kind;/* STFT frames or ready cross spectra */
     int32_t max_frames;       /* largest L a call may pass, >= 1 */
-    int32_t host_io;          /* nonzero: also size staging buffers for srp_map_host */
+    int32_t host_io;          /* staging slots for the host entry points: 0 none,
+                                 1 for srp_map_host, 2 also for srp_map_host_async */
     srp_engine engine;        /* which units run the map contraction */
 } srp_plan_desc;
 
@@ -167,6 +168,23 @@ SRP_API srp_status srp_map(srp_handle h, const void *d_in, int32_t L, float *d_m
  * built with host_io != 0.  h_maps and h_peak may be NULL.                */
 SRP_API srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps,
                         int32_t *h_argmax, float *h_peak, srp_stream_t s);
+
+/* Pipelined host entry point (plan built with host_io = 2): enqueues the
+ * copy of h_in to one of two device staging slots on an internal copy
+ * stream, the map on stream s, and the copies of the results back to h_maps
+ * (may be NULL), h_argmax and h_peak (may be NULL) on a second internal copy
+ * stream, ordered by events, and returns without waiting.  Consecutive calls
+ * alternate the slots, so the copies of one call overlap the maps of its
+ * neighbours; the maps themselves run in order on s.  h_in must stay
+ * unchanged and the result buffers untouched until srp_map_host_wait
+ * returns (pinned host memory keeps the copies asynchronous).  Do not mix
+ * with srp_map_host on the same plan without a srp_map_host_wait between.  */
+SRP_API srp_status srp_map_host_async(srp_handle h, const void *h_in, int32_t L, float *h_maps,
+                                      int32_t *h_argmax, float *h_peak, srp_stream_t s);
+
+/* Wait until every srp_map_host_async call on h has delivered its results,
+ * then poll the device status as srp_poll_device_status does.            */
+SRP_API srp_status srp_map_host_wait(srp_handle h);
 
 /* First stage alone: PHAT cross spectra psi[L][Q][Kb] complex64 from STFT
  * frames y[L][M][Kb] (Eq. corrmatrix with the PHAT weight of Sec. 2.1).

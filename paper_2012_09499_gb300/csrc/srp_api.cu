@@ -159,11 +159,13 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     lay.b_ctab = lay.tc ? sizeof(int4) * (size_t)lay.n_chunks : 0;
     lay.b_status = sizeof(int);
     lay.b_part = sizeof(unsigned long long) * (size_t)lay.L_pad * lay.n_tiles;
-    if (d->host_io) {
+    if (d->host_io < 0 || d->host_io > 2) return fail(SRP_ERR_INVALID_ARG, "host_io must be 0, 1 or 2");
+    if (d->host_io) {  // host_io staging slots, each 256-byte aligned
         const int rows = d->input_kind == SRP_IN_STFT ? lay.M : lay.Q;
-        lay.b_in_stage = sizeof(float2) * (size_t)lay.L_max * rows * lay.Kb;
-        lay.b_maps_stage = sizeof(float) * (size_t)lay.L_max * (size_t)lay.J;
-        lay.b_small_stage = 2 * sizeof(float) * (size_t)lay.L_pad;
+        const size_t slots = (size_t)d->host_io;
+        lay.b_in_stage = slots * round_up(sizeof(float2) * (size_t)lay.L_max * rows * lay.Kb, 256);
+        lay.b_maps_stage = slots * round_up(sizeof(float) * (size_t)lay.L_max * (size_t)lay.J, 256);
+        lay.b_small_stage = slots * 2 * round_up(sizeof(float) * (size_t)lay.L_pad, 256);
     }
     return SRP_OK;
 }
@@ -223,6 +225,13 @@ void release(srp_plan_s *h) {
     cudaFree(h->d_peak_stage);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k) {
+        if (h->ev_in[k]) cudaEventDestroy(h->ev_in[k]);
+        if (h->ev_done[k]) cudaEventDestroy(h->ev_done[k]);
+        if (h->ev_out[k]) cudaEventDestroy(h->ev_out[k]);
+    }
+    if (h->io_in) cudaStreamDestroy(h->io_in);
+    if (h->io_out) cudaStreamDestroy(h->io_out);
 }
 
 // Build the TDOA table in FP64 (Eq. Deltat_i / Eq. Deltat_i_spher), convert
@@ -477,10 +486,21 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     SRP_ALLOC(h->d_status, L.b_status);
     SRP_ALLOC(h->d_part, L.b_part);
     if (h->host_io) {
+        h->n_slots = h->host_io;
         SRP_ALLOC(h->d_in_stage, L.b_in_stage);
         SRP_ALLOC(h->d_maps_stage, L.b_maps_stage);
         SRP_ALLOC(h->d_argmax_stage, L.b_small_stage / 2);
         SRP_ALLOC(h->d_peak_stage, L.b_small_stage / 2);
+    }
+    if (h->n_slots == 2) {
+        if ((e = cudaStreamCreateWithFlags(&h->io_in, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&h->io_out, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaStreamCreate"));
+        for (int k = 0; k < 2; ++k)
+            if ((e = cudaEventCreateWithFlags(&h->ev_in[k], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&h->ev_done[k], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&h->ev_out[k], cudaEventDisableTiming)) != cudaSuccess)
+                return bail(cuda_fail(e, "cudaEventCreate"));
     }
 #undef SRP_ALLOC
     std::vector<int2> pairs(L.Q);
@@ -582,7 +602,7 @@ srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps
     SRP_CUDA(cudaMemcpyAsync(h->d_in_stage, h_in, in_bytes, cudaMemcpyHostToDevice, cs),
              "copy input to device");
     st = run_map(h, h->d_in_stage, L, h_maps ? h->d_maps_stage : nullptr, h->d_argmax_stage,
-                 h->d_peak_stage, cs);
+                 h->d_peak_stage, cs);  // slot 0
     if (st != SRP_OK) return st;
     if (h_maps)
         SRP_CUDA(cudaMemcpyAsync(h_maps, h->d_maps_stage, sizeof(float) * (size_t)L * lay.J,
@@ -594,6 +614,81 @@ srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps
                                  cudaMemcpyDeviceToHost, cs), "copy peak to host");
     SRP_CUDA(cudaStreamSynchronize(cs), "synchronise stream");
     return srp_poll_device_status(h, s);
+}
+
+// Byte offsets of staging slot k (see make_layout: slots are 256-byte aligned).
+struct SlotPtrs {
+    char *in;
+    float *maps;
+    int32_t *argmax;
+    float *peak;
+};
+
+static SlotPtrs slot_ptrs(srp_plan_s *h, int k) {
+    const Layout &lay = h->lay;
+    const size_t n = (size_t)h->n_slots;
+    SlotPtrs p;
+    p.in = static_cast<char *>(h->d_in_stage) + k * (lay.b_in_stage / n);
+    p.maps = reinterpret_cast<float *>(reinterpret_cast<char *>(h->d_maps_stage) +
+                                       k * (lay.b_maps_stage / n));
+    p.argmax = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(h->d_argmax_stage) +
+                                           k * (lay.b_small_stage / 2 / n));
+    p.peak = reinterpret_cast<float *>(reinterpret_cast<char *>(h->d_peak_stage) +
+                                       k * (lay.b_small_stage / 2 / n));
+    return p;
+}
+
+srp_status srp_map_host_async(srp_handle h, const void *h_in, int32_t L, float *h_maps,
+                              int32_t *h_argmax, float *h_peak, srp_stream_t s) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (h->n_slots != 2) return fail(SRP_ERR_INVALID_ARG, "plan was not built with host_io = 2");
+    if (L < 0 || L > h->lay.L_max) return fail(SRP_ERR_INVALID_ARG, "L out of [0, max_frames]");
+    if (L == 0) return SRP_OK;
+    if (h_in == nullptr || h_argmax == nullptr)
+        return fail(SRP_ERR_INVALID_ARG, "h_in and h_argmax must be non-NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+    const Layout &lay = h->lay;
+    const int k = h->next_slot;
+    h->next_slot ^= 1;
+    const SlotPtrs sp = slot_ptrs(h, k);
+    const int rows = h->input_kind == SRP_IN_STFT ? lay.M : lay.Q;
+    const size_t in_bytes = sizeof(float2) * (size_t)L * rows * lay.Kb;
+    // input: once the slot's previous map has read it
+    SRP_CUDA(cudaStreamWaitEvent(h->io_in, h->ev_done[k], 0), "order input copy");
+    SRP_CUDA(cudaMemcpyAsync(sp.in, h_in, in_bytes, cudaMemcpyHostToDevice, h->io_in),
+             "copy input to device");
+    SRP_CUDA(cudaEventRecord(h->ev_in[k], h->io_in), "record input copy");
+    // map: once the input is in and the slot's previous results have left
+    SRP_CUDA(cudaStreamWaitEvent(cs, h->ev_in[k], 0), "order map");
+    SRP_CUDA(cudaStreamWaitEvent(cs, h->ev_out[k], 0), "order map");
+    st = run_map(h, sp.in, L, h_maps ? sp.maps : nullptr, sp.argmax, sp.peak, cs);
+    if (st != SRP_OK) return st;
+    SRP_CUDA(cudaEventRecord(h->ev_done[k], cs), "record map");
+    // results
+    SRP_CUDA(cudaStreamWaitEvent(h->io_out, h->ev_done[k], 0), "order result copy");
+    if (h_maps)
+        SRP_CUDA(cudaMemcpyAsync(h_maps, sp.maps, sizeof(float) * (size_t)L * lay.J,
+                                 cudaMemcpyDeviceToHost, h->io_out), "copy maps to host");
+    SRP_CUDA(cudaMemcpyAsync(h_argmax, sp.argmax, sizeof(int32_t) * L, cudaMemcpyDeviceToHost,
+                             h->io_out), "copy argmax to host");
+    if (h_peak)
+        SRP_CUDA(cudaMemcpyAsync(h_peak, sp.peak, sizeof(float) * L, cudaMemcpyDeviceToHost,
+                                 h->io_out), "copy peak to host");
+    SRP_CUDA(cudaEventRecord(h->ev_out[k], h->io_out), "record result copy");
+    return SRP_OK;
+}
+
+srp_status srp_map_host_wait(srp_handle h) {
+    srp_status st = check_handle(h);
+    if (st != SRP_OK) return st;
+    if (h->n_slots != 2) return fail(SRP_ERR_INVALID_ARG, "plan was not built with host_io = 2");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
+    SRP_CUDA(cudaStreamSynchronize(h->io_out), "wait for results");
+    return srp_poll_device_status(h, reinterpret_cast<srp_stream_t>(h->io_out));
 }
 
 srp_status srp_poll_device_status(srp_handle h, srp_stream_t s) {

@@ -66,11 +66,16 @@ struct srp_plan_s {
     int *d_status = nullptr;       // device error flags (bit 0: a bounded wait gave up)
     alignas(64) unsigned char xi_map[128] = {};  // CUtensorMap of d_xi16
     unsigned long long *d_part = nullptr;  // [L_pad][n_tiles] per-tile argmax keys
-    // staging for srp_map_host (owned, optional)
+    // staging for srp_map_host (slot 0) and srp_map_host_async (slots 0, 1)
+    // (owned, optional): n_slots consecutive slots per buffer
+    int n_slots = 0;
     void *d_in_stage = nullptr;
     float *d_maps_stage = nullptr;
     int32_t *d_argmax_stage = nullptr;
     float *d_peak_stage = nullptr;
+    cudaStream_t io_in = nullptr, io_out = nullptr;  // copy streams of srp_map_host_async
+    cudaEvent_t ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {};
+    int next_slot = 0;
     // timing
     int timing = 0;
     cudaEvent_t ev[srp::kNumStages + 1] = {};

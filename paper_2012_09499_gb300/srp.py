@@ -106,6 +106,8 @@ def lib():
             "srp_plan_tdoa": [vp, vp],
             "srp_map": [vp, vp, i32, vp, vp, vp, vp],
             "srp_map_host": [vp, vp, i32, vp, vp, vp, vp],
+            "srp_map_host_async": [vp, vp, i32, vp, vp, vp, vp],
+            "srp_map_host_wait": [vp],
             "srp_cross_spectra": [vp, vp, i32, vp, vp],
             "srp_gcc_samples": [vp, vp, i32, vp, vp],
             "srp_set_timing": [vp, i32],
@@ -191,7 +193,7 @@ def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="f
     d.precision = PRECISIONS[precision]
     d.input_kind = INPUTS[input_kind]
     d.max_frames = int(max_frames)
-    d.host_io = 1 if host_io else 0
+    d.host_io = int(host_io)  # 0, 1 (srp_map_host) or 2 (also srp_map_host_async)
     d.engine = ENGINES[engine]
     return d, (mic, grid)
 
@@ -238,6 +240,16 @@ def srp_map_host(h, h_in, L, h_maps, h_argmax, h_peak=None, stream=None):
     _check(lib().srp_map_host(h, _host_ptr(h_in), int(L), _host_ptr(h_maps),
                               _host_ptr(h_argmax), _host_ptr(h_peak), _stream(stream)),
            "srp_map_host")
+
+
+def srp_map_host_async(h, h_in, L, h_maps, h_argmax, h_peak=None, stream=None):
+    _check(lib().srp_map_host_async(h, _host_ptr(h_in), int(L), _host_ptr(h_maps),
+                                    _host_ptr(h_argmax), _host_ptr(h_peak), _stream(stream)),
+           "srp_map_host_async")
+
+
+def srp_map_host_wait(h):
+    _check(lib().srp_map_host_wait(h), "srp_map_host_wait")
 
 
 def srp_cross_spectra(h, d_y, L, d_psi, stream=None):

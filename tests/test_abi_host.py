@@ -117,7 +117,7 @@ def test_footprint_counts_every_buffer():
 @pytest.mark.parametrize("field,value", [
     ("M", 1), ("M", 65), ("K", 7), ("K", 2), ("K", 16384), ("J", 0), ("fs", 0.0),
     ("c", -1.0), ("n_aux", -1), ("max_frames", 0), ("mode", 3), ("precision", 7),
-    ("input_kind", 5), ("grid_kind", 4), ("engine", 2),
+    ("input_kind", 5), ("grid_kind", 4), ("engine", 2), ("host_io", 3), ("host_io", -1),
 ])
 def test_invalid_descriptors_rejected(field, value):
     d, keep = _desc()
@@ -204,3 +204,15 @@ def test_server_entry_points_reject_bad_arguments():
     assert L.srp_server_submit(None, 0, None, 1, None, None, None, 0, 0.0, None) == \
         srp.SRP_ERR_INVALID_ARG
     assert L.srp_server_destroy(None) == srp.SRP_OK
+
+
+def test_footprint_counts_host_staging_slots():
+    """host_io slots of staging: input, maps, argmax and peak per slot, each
+    rounded up to 256 bytes."""
+    up = lambda v: -(-v // 256) * 256
+    d0, k0 = _desc(M=6, J=1000, K=512, max_frames=20)
+    base = srp.srp_plan_footprint(d0)
+    for slots in (1, 2):
+        d, k = _desc(M=6, J=1000, K=512, max_frames=20, host_io=slots)
+        stage = up(8 * 20 * 6 * 257) + up(4 * 20 * 1000) + 2 * up(4 * 32)
+        assert srp.srp_plan_footprint(d) == base + slots * stage
