@@ -253,3 +253,31 @@ def uneven_instance(seed: int, J_range=(10_000, 500_000), L: int = 32, dims=None
 def uneven_mix(seed: int, n: int, J_range=(10_000, 500_000), L: int = 32) -> list:
     """n arrays of the uneven mix (uneven_instance with seeds derived from seed)."""
     return [uneven_instance(seed * 100_003 + i, J_range, L) for i in range(n)]
+
+
+def random_lower_direction(rng: np.random.Generator) -> np.ndarray:
+    """A unit vector of the far-field candidate family of Sec. 4,
+    -(sin t cos p, sin t sin p, cos t), with t uniform in [90, 180) degrees and
+    p uniform in [0, 360) degrees (so it generally falls between grid points)."""
+    t = np.deg2rad(rng.uniform(90.0, 180.0))
+    p = np.deg2rad(rng.uniform(0.0, 360.0))
+    return -np.array([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)])
+
+
+def paper_circle_setup(seed: int, L: int = 32, K: int = 2048, step_deg: float = 2.0,
+                       snr_range=(-3.0, 6.0)) -> dict:
+    """The paper's evaluation geometry (Sec. 4) with synthetic signals: M = 6
+    microphones on a circle of radius 0.1 m, far-field candidates on the lower
+    half sphere at 2 degrees (J = 8101), fs = 16 kHz (omega_0 / 2 pi = 8 kHz),
+    K = 2048 with a square-root Hann window.  One white plane-wave source
+    from a random direction, with white sensor noise at an SNR uniform in
+    snr_range (the paper's babble-noise SNRs; reverberation and speech are not
+    modelled)."""
+    rng = np.random.default_rng(seed)
+    mic = circular_array(6, 0.1)
+    grid = half_sphere_directions(step_deg)
+    u = random_lower_direction(rng)
+    snr = float(rng.uniform(*snr_range))
+    Y = free_field_stft(rng, mic, [u], 16000.0, K, L, snr, far_field=True)
+    return dict(mic=mic, grid=grid, fs=16000.0, c=C_SOUND, K=K, L=L, Y=Y, sources=u[None, :],
+                far_field=True, snr_db=snr, name="paper_circle")
