@@ -59,6 +59,7 @@ def _load():
             lib.orc_tdoa_points.argtypes = [i32, f64p, i64, f64p, f64, f64, f64p]
             lib.orc_tdoa_directions.argtypes = [i32, f64p, i64, f64p, f64, f64, f64p]
             lib.orc_phat.argtypes = [i64, i32, i32, f64p, f64p]
+            lib.orc_cross_power.argtypes = [i64, i32, i32, f64p, f64p]
             lib.orc_conventional.argtypes = [i64, i32, i32, f64p, i64, f64p, f64p]
             lib.orc_gcc_samples.argtypes = [i64, i32, i32, f64p, i32p, i32, f64p]
             lib.orc_nyquist.argtypes = [i64, i32, i32p, i32, f64p, i64, f64p, f64p]
@@ -127,6 +128,22 @@ def phat(Y):
     return psi[..., 0] + 1j * psi[..., 1]
 
 
+def cross_power(Y):
+    """Unweighted cross spectra psi[L][Q][Kb] = y_m conj(y_m') (Eq. corrmatrix
+    without a GCC weighting)."""
+    Y = np.asarray(Y)
+    L, M, Kb = Y.shape
+    Q = M * (M - 1) // 2
+    psi = np.zeros((L, Q, Kb, 2), np.float64)
+    _load().orc_cross_power(L, M, Kb, _c64(_cplx_to_f64(Y)), psi)
+    return psi[..., 0] + 1j * psi[..., 1]
+
+
+def cross_spectra(Y, weighting="phat"):
+    """PHAT-weighted (default) or unweighted cross spectra of STFT frames."""
+    return phat(Y) if weighting == "phat" else cross_power(Y)
+
+
 def conventional(psi, x, K: int):
     """Conventional SRP map[L][J] from psi[L][Q][Kb] and TDOAs x[J][Q] (Sec. 2.4)."""
     psi = np.asarray(psi)
@@ -183,14 +200,14 @@ def e_appr_db(srp, srp_appr):
 
 
 def srp_map(Y, mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2,
-            far_field=False, psi=None):
+            far_field=False, psi=None, weighting="phat"):
     """Whole path for one block of frames: returns (maps[L][J], argmax[L], peak[L]).
 
     ``Y`` are STFT frames [L][M][Kb]; pass ``psi`` instead to start from
     already weighted cross spectra [L][Q][Kb]."""
     x = tdoa(mic_xyz, grid_xyz, fs, c, far_field)
     if psi is None:
-        psi = phat(Y)
+        psi = cross_spectra(Y, weighting)
     if mode == "conventional":
         maps = conventional(psi, x, K)
     elif mode == "nyquist":

@@ -157,6 +157,27 @@ void orc_phat(int64_t L, int M, int Kb, const double *Y, double *psi) {
     free(mp_of_q);
 }
 
+/* Unweighted cross spectra (Eq. corrmatrix without a GCC weighting; Sec. 2.1
+ * notes that the method holds for any weighting): psi_q(k) = y_m(k) y_m'(k)^*
+ * for the pair q = (m, m').  Same layout as orc_phat. */
+void orc_cross_power(int64_t L, int M, int Kb, const double *Y, double *psi) {
+    int Q = orc_num_pairs(M);
+    int32_t *m_of_q = malloc(sizeof(int32_t) * Q), *mp_of_q = malloc(sizeof(int32_t) * Q);
+    orc_pairs(M, m_of_q, mp_of_q);
+#pragma omp parallel for schedule(static) num_threads(nthreads())
+    for (int64_t l = 0; l < L; ++l)
+        for (int q = 0; q < Q; ++q)
+            for (int k = 0; k < Kb; ++k) {
+                const double *ym = &Y[2 * ((l * M + m_of_q[q]) * Kb + k)];
+                const double *ymp = &Y[2 * ((l * M + mp_of_q[q]) * Kb + k)];
+                double *out = &psi[2 * ((l * Q + q) * Kb + k)];
+                out[0] = ym[0] * ymp[0] + ym[1] * ymp[1];
+                out[1] = ym[1] * ymp[0] - ym[0] * ymp[1];
+            }
+    free(m_of_q);
+    free(mp_of_q);
+}
+
 /* Bin weight of the one-sided discretisation of the two-sided integral. */
 static double bin_weight(int k, int K) { return (k == 0 || 2 * k == K) ? 1.0 : 2.0; }
 

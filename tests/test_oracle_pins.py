@@ -336,3 +336,37 @@ def test_argmax_first_maximum():
     idx, val = oracle.argmax(maps)
     assert idx.tolist() == [1, 0, 0]
     assert val.tolist() == [2.0, -1.0, 5.0]
+
+
+def test_unweighted_cross_power_closed_form():
+    """No GCC weighting (Sec. 2.1: the method holds for any weighting).  In
+    noiseless free field with exact circular delays every pair's cross
+    spectrum is in phase at the source, so the conventional map there equals
+    (1/K) sum_q sum_k a_k |y_m(k)| |y_m'(k)| and is the maximum; the
+    unweighted map scales with the square of an input gain, the PHAT map not
+    at all; and the unweighted cross spectrum of one pair and bin is
+    y_m conj(y_m')."""
+    rng = np.random.default_rng(12)
+    mic = synth.square_array_2d(0.2)
+    grid = synth.plane_grid(4.0, 41)
+    fs, c, K, L = 16000.0, 343.0, 256, 2
+    src = int(np.argmin(np.linalg.norm(grid - np.array([1.1, -0.7, 0.0]), axis=1)))
+    Y = synth.circular_frames(rng, mic, grid[src], fs, K, L).astype(np.complex128)
+    args = (mic, grid, fs, c, K)
+    maps, idx, val = oracle.srp_map(Y, *args, mode="conventional", weighting="none")
+    Kb = K // 2 + 1
+    a = np.full(Kb, 2.0)
+    a[0] = a[-1] = 1.0
+    A = np.abs(Y.astype(np.complex128))
+    expect = [sum(np.sum(a * A[l, m] * A[l, mp]) for mp in range(4) for m in range(mp + 1, 4)) / K
+              for l in range(L)]
+    assert np.all(idx == src)
+    np.testing.assert_allclose(val, expect, rtol=1e-12)
+    m3, _, _ = oracle.srp_map(3.0 * Y, *args, mode="conventional", weighting="none")
+    np.testing.assert_allclose(m3, 9.0 * maps, rtol=1e-12, atol=1e-11 * np.abs(maps).max())
+    p1, _, _ = oracle.srp_map(Y, *args, mode="conventional")
+    p3, _, _ = oracle.srp_map(3.0 * Y, *args, mode="conventional")
+    np.testing.assert_allclose(p3, p1, rtol=1e-12, atol=1e-12)
+    psi = oracle.cross_power(Y)  # pairs m' = 0..M-2 outer, m > m' inner: q = 3 is (2, 1)
+    np.testing.assert_allclose(psi[1, 3, 7], complex(Y[1, 2, 7]) * np.conj(complex(Y[1, 1, 7])),
+                               rtol=1e-12)
