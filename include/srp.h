@@ -89,6 +89,13 @@ typedef enum {
 } srp_input_kind;
 
 typedef enum {
+    SRP_WEIGHT_PHAT = 0, /* PHAT weighting: psi = y_m y_m'^* / |y_m y_m'^*| (Sec. 2.1) */
+    SRP_WEIGHT_NONE = 1  /* no weighting: psi = y_m y_m'^* (plain cross power; the
+                            method holds for any weighting, Sec. 2.1).  With
+                            single-frame spectra the SCOT weighting equals PHAT */
+} srp_weighting;
+
+typedef enum {
     SRP_ENGINE_AUTO = 0,      /* tensor cores (tcgen05) where built, else CUDA cores */
     SRP_ENGINE_CUDA_CORES = 1 /* FP32 CUDA-core kernels only (FP32 precision) */
 } srp_engine;
@@ -110,6 +117,9 @@ typedef struct {
     int32_t host_io;          /* staging slots for the host entry points: 0 none,
                                  1 for srp_map_host, 2 also for srp_map_host_async */
     srp_engine engine;        /* which units run the map contraction */
+    srp_weighting weighting;  /* GCC weighting of STFT input (ignored for cross spectra);
+                                 SRP_WEIGHT_NONE is not available with SRP_PREC_FP16,
+                                 whose range unnormalised spectra can exceed */
 } srp_plan_desc;
 
 /* Sizes of a plan, computed on the host (no device needed). */
@@ -186,8 +196,8 @@ SRP_API srp_status srp_map_host_async(srp_handle h, const void *h_in, int32_t L,
  * then poll the device status as srp_poll_device_status does.            */
 SRP_API srp_status srp_map_host_wait(srp_handle h);
 
-/* First stage alone: PHAT cross spectra psi[L][Q][Kb] complex64 from STFT
- * frames y[L][M][Kb] (Eq. corrmatrix with the PHAT weight of Sec. 2.1).
+/* First stage alone: cross spectra psi[L][Q][Kb] complex64 from STFT
+ * frames y[L][M][Kb] (Eq. corrmatrix with the plan's GCC weighting, Sec. 2.1).
  * Plan must take SRP_IN_STFT.  Asynchronous on s.                         */
 SRP_API srp_status srp_cross_spectra(srp_handle h, const void *d_y, int32_t L, void *d_psi,
                              srp_stream_t s);

@@ -60,6 +60,11 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         return fail(SRP_ERR_INVALID_ARG, "unknown grid kind");
     if (d->engine != SRP_ENGINE_AUTO && d->engine != SRP_ENGINE_CUDA_CORES)
         return fail(SRP_ERR_INVALID_ARG, "unknown engine");
+    if (d->weighting != SRP_WEIGHT_PHAT && d->weighting != SRP_WEIGHT_NONE)
+        return fail(SRP_ERR_INVALID_ARG, "unknown weighting");
+    if (d->weighting == SRP_WEIGHT_NONE && d->precision == SRP_PREC_FP16 &&
+        d->input_kind == SRP_IN_STFT)
+        return fail(SRP_ERR_UNSUPPORTED, "unweighted spectra can exceed the FP16 range");
     if (d->max_frames < 1 || d->max_frames > kMaxFrames)
         return fail(SRP_ERR_INVALID_ARG, "max_frames must be in [1, 65536]");
     for (int m = 0; m < d->M; ++m)
@@ -358,7 +363,7 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     const float2 *psi = static_cast<const float2 *>(d_in);
     if (h->input_kind == SRP_IN_STFT) {
         SRP_CUDA(launch_phat(static_cast<const float2 *>(d_in), L, lay.M, lay.Kb, h->d_pairs,
-                             lay.Q, h->d_psi, s), "PHAT kernel");
+                             lay.Q, h->weighting, h->d_psi, s), "cross-spectrum kernel");
         psi = h->d_psi;
         h->stage_ran[kStagePhat] = 1;
         ++launches;
@@ -458,6 +463,7 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     h->mode = d->mode;
     h->precision = d->precision;
     h->input_kind = d->input_kind;
+    h->weighting = d->weighting;
     h->host_io = d->host_io;
     const Layout &L = h->lay;
     auto bail = [&](srp_status s) {
@@ -718,8 +724,9 @@ srp_status srp_cross_spectra(srp_handle h, const void *d_y, int32_t L, void *d_p
     if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plan's device");
     const Layout &lay = h->lay;
     SRP_CUDA(launch_phat(static_cast<const float2 *>(d_y), L, lay.M, lay.Kb, h->d_pairs, lay.Q,
-                         static_cast<float2 *>(d_psi), reinterpret_cast<cudaStream_t>(s)),
-             "PHAT kernel");
+                         h->weighting, static_cast<float2 *>(d_psi),
+                         reinterpret_cast<cudaStream_t>(s)),
+             "cross-spectrum kernel");
     return SRP_OK;
 }
 
@@ -737,7 +744,7 @@ srp_status srp_gcc_samples(srp_handle h, const void *d_in, int32_t L, float *d_x
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
     const float2 *psi = static_cast<const float2 *>(d_in);
     if (h->input_kind == SRP_IN_STFT) {
-        SRP_CUDA(launch_phat(psi, L, lay.M, lay.Kb, h->d_pairs, lay.Q, h->d_psi, cs),
+        SRP_CUDA(launch_phat(psi, L, lay.M, lay.Kb, h->d_pairs, lay.Q, h->weighting, h->d_psi, cs),
                  "PHAT kernel");
         psi = h->d_psi;
     }

@@ -61,6 +61,7 @@ struct BatchInst {
     int64_t J, J_pad;
     int64_t b_row0;           // first row of the plan's block of operand B
     int M, Q, K, n_aux, xf, n_chunks, n_tiles, par1_used, input_kind, Lb, max_frames;
+    int weighting;            // srp_weighting of STFT input
     int pblocks;              // pair blocks of kPairBlock per frame
     int64_t op_row0;          // first block of the plan in the operand kernel's grid
     int64_t frame0;           // first block of the plan in the argmax kernel's grid
@@ -138,8 +139,10 @@ __global__ void __launch_bounds__(128) k_batch_operands(const BatchInst *__restr
         const int q = q0 + j;
         if (I.input_kind == SRP_IN_STFT) {
             const int2 pr = I.pairs[q];
-            return phat_cross(unit_phase(in[((size_t)l * I.M + pr.x) * Kb + k]),
-                              unit_phase(in[((size_t)l * I.M + pr.y) * Kb + k]));
+            const float2 ym = in[((size_t)l * I.M + pr.x) * Kb + k];
+            const float2 ymp = in[((size_t)l * I.M + pr.y) * Kb + k];
+            if (I.weighting == SRP_WEIGHT_NONE) return times_conj(ym, ymp);  // y_m y_m'^*
+            return times_conj(unit_phase(ym), unit_phase(ymp));
         }
         return in[((size_t)l * Q + q) * Kb + k];
     };
@@ -990,6 +993,7 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         I.n_tiles = L.n_tiles;
         I.par1_used = L.par1_used;
         I.input_kind = p->input_kind;
+        I.weighting = p->weighting;
         I.max_frames = L.L_max;
         I.pblocks = (L.Q + kPairBlock - 1) / kPairBlock;
         part += sizeof(unsigned long long) * (size_t)L.L_max * L.n_tiles;

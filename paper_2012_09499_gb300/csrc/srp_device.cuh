@@ -138,9 +138,10 @@ __device__ __forceinline__ void gcc_row(const float2 *tw, const float2 *ps, int 
              [&](int, int t, int n, float v) { emit(t, n, v); });
 }
 
-// PHAT cross spectrum of one bin: u_m conj(u_m') with u = y / |y| (0 where
-// y = 0), which equals y_m y_m'^* / |y_m y_m'^*| without forming the product
-// of two small magnitudes.
+// PHAT cross spectrum of one bin: times_conj(unit_phase(y_m), unit_phase(y_m'))
+// = u_m conj(u_m') with u = y / |y| (0 where y = 0), which equals
+// y_m y_m'^* / |y_m y_m'^*| without forming the product of two small
+// magnitudes; times_conj(y_m, y_m') is the unweighted cross spectrum.
 __device__ __forceinline__ float2 unit_phase(float2 v) {
     const float a2 = fmaf(v.x, v.x, v.y * v.y);
     if (a2 > 1e-30f && a2 < 1e30f) {  // the usual case: one reciprocal square root
@@ -151,7 +152,8 @@ __device__ __forceinline__ float2 unit_phase(float2 v) {
     return a > 0.0f ? make_float2(v.x / a, v.y / a) : make_float2(0.0f, 0.0f);
 }
 
-__device__ __forceinline__ float2 phat_cross(float2 a, float2 b) {
+// a conj(b)
+__device__ __forceinline__ float2 times_conj(float2 a, float2 b) {
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 

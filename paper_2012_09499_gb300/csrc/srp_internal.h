@@ -48,6 +48,7 @@ struct srp_plan_s {
     srp_mode mode = SRP_MODE_NYQUIST;
     srp_precision precision = SRP_PREC_FP32;
     srp_input_kind input_kind = SRP_IN_STFT;
+    srp_weighting weighting = SRP_WEIGHT_PHAT;
     int host_io = 0;
     srp::Layout lay;
     // device tables (owned)
@@ -115,7 +116,7 @@ struct DeviceGuard {
 
 // ---- kernel launchers (srp_kernels.cu); each returns cudaGetLastError() ----
 cudaError_t launch_phat(const float2 *y, int L, int M, int Kb, const int2 *pairs, int Q,
-                        float2 *psi, cudaStream_t s);
+                        int weighting, float2 *psi, cudaStream_t s);
 cudaError_t launch_gcc_samples(const float2 *psi, int L, int Q, int K, const int32_t *nq,
                                const int32_t *off, int n_aux, const float2 *twid, float *xi,
                                int64_t s_stride, int64_t l_stride, cudaStream_t s);

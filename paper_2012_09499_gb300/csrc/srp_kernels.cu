@@ -20,20 +20,24 @@ using namespace dev;
 // ---------------------------------------------------------------------------
 // K1: psi_q(k) = u_m(k) conj(u_m'(k)) with u = y / |y| (0 where y = 0).  That
 // equals y_m y_m'^* / |y_m y_m'^*| and never forms the product of two small
-// magnitudes.  One CTA: one frame, kPhatBins bins, all microphones and pairs.
+// magnitudes.  Without a weighting, u = y.  One CTA: one frame, kPhatBins
+// bins, all microphones and pairs.
 // ---------------------------------------------------------------------------
 constexpr int kPhatBins = 64;
 
 __global__ void __launch_bounds__(256) k_phat(const float2 *__restrict__ y, int M, int Kb,
                                               const int2 *__restrict__ pairs, int Q,
-                                              float2 *__restrict__ psi) {
+                                              int weighting, float2 *__restrict__ psi) {
     extern __shared__ float2 u_sm[];  // [M][kPhatBins]
     const int l = blockIdx.y;
     const int k0 = blockIdx.x * kPhatBins;
     for (int e = threadIdx.x; e < M * kPhatBins; e += blockDim.x) {
         const int m = e / kPhatBins, k = k0 + e % kPhatBins;
         float2 v = make_float2(0.0f, 0.0f);
-        if (k < Kb) v = unit_phase(y[((size_t)l * M + m) * Kb + k]);
+        if (k < Kb) {
+            v = y[((size_t)l * M + m) * Kb + k];
+            if (weighting == SRP_WEIGHT_PHAT) v = unit_phase(v);
+        }
         u_sm[e] = v;
     }
     __syncthreads();
@@ -42,7 +46,7 @@ __global__ void __launch_bounds__(256) k_phat(const float2 *__restrict__ y, int 
         if (k >= Kb) continue;
         const int2 p = pairs[q];
         psi[((size_t)l * Q + q) * Kb + k] =
-            phat_cross(u_sm[p.x * kPhatBins + kk], u_sm[p.y * kPhatBins + kk]);
+            times_conj(u_sm[p.x * kPhatBins + kk], u_sm[p.y * kPhatBins + kk]);
     }
 }
 
@@ -252,10 +256,10 @@ constexpr int kFramesPerCta = 16;
 }  // namespace
 
 cudaError_t launch_phat(const float2 *y, int L, int M, int Kb, const int2 *pairs, int Q,
-                        float2 *psi, cudaStream_t s) {
+                        int weighting, float2 *psi, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
     dim3 grid((Kb + kPhatBins - 1) / kPhatBins, L);
-    k_phat<<<grid, 256, sizeof(float2) * M * kPhatBins, s>>>(y, M, Kb, pairs, Q, psi);
+    k_phat<<<grid, 256, sizeof(float2) * M * kPhatBins, s>>>(y, M, Kb, pairs, Q, weighting, psi);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ MODES = {"conventional": 1, "nyquist": 2}
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 INPUTS = {"stft": 0, "cross": 1}
 ENGINES = {"auto": 0, "cuda_cores": 1}
+WEIGHTINGS = {"phat": 0, "none": 1}
 STAGES = ("cross_spectra", "gcc_samples", "map", "argmax")
 
 
@@ -38,7 +39,7 @@ class srp_plan_desc(ctypes.Structure):
         ("fs", ctypes.c_double), ("c", ctypes.c_double), ("K", ctypes.c_int32),
         ("mode", ctypes.c_int), ("n_aux", ctypes.c_int32), ("precision", ctypes.c_int),
         ("input_kind", ctypes.c_int), ("max_frames", ctypes.c_int32),
-        ("host_io", ctypes.c_int32), ("engine", ctypes.c_int),
+        ("host_io", ctypes.c_int32), ("engine", ctypes.c_int), ("weighting", ctypes.c_int),
     ]
 
 
@@ -177,7 +178,8 @@ def _stream(s):
 
 
 def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="fp32",
-              input_kind="stft", max_frames=64, far_field=False, host_io=False, engine="auto"):
+              input_kind="stft", max_frames=64, far_field=False, host_io=False, engine="auto",
+              weighting="phat"):
     """Fill an srp_plan_desc; returns (desc, keep-alive arrays)."""
     mic = np.ascontiguousarray(mic_xyz, np.float64)
     grid = np.ascontiguousarray(grid_xyz, np.float64)
@@ -195,6 +197,7 @@ def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="f
     d.max_frames = int(max_frames)
     d.host_io = int(host_io)  # 0, 1 (srp_map_host) or 2 (also srp_map_host_async)
     d.engine = ENGINES[engine]
+    d.weighting = WEIGHTINGS[weighting]
     return d, (mic, grid)
 
 

@@ -118,6 +118,7 @@ def test_footprint_counts_every_buffer():
     ("M", 1), ("M", 65), ("K", 7), ("K", 2), ("K", 16384), ("J", 0), ("fs", 0.0),
     ("c", -1.0), ("n_aux", -1), ("max_frames", 0), ("mode", 3), ("precision", 7),
     ("input_kind", 5), ("grid_kind", 4), ("engine", 2), ("host_io", 3), ("host_io", -1),
+    ("weighting", 2),
 ])
 def test_invalid_descriptors_rejected(field, value):
     d, keep = _desc()
@@ -128,7 +129,8 @@ def test_invalid_descriptors_rejected(field, value):
 
 
 @pytest.mark.parametrize("kw", [dict(mode="conventional", precision="bf16", engine="cuda_cores"),
-                                dict(engine="cuda_cores", precision="fp16")])
+                                dict(engine="cuda_cores", precision="fp16"),
+                                dict(precision="fp16", weighting="none")])
 def test_half_precision_needs_tensor_cores(kw):
     d, keep = _desc(**kw)
     with pytest.raises(srp.SrpError) as e:

@@ -214,3 +214,17 @@ def test_batch_timing_mode_same_outputs():
     for (m0, a0, _), (m1, a1, _) in zip(graph, timed):
         assert np.array_equal(m0, m1) and np.array_equal(a0, a1)
     batch.close()
+
+
+def test_batch_mixes_weightings():
+    """A batch may hold PHAT and unweighted plans (the weighting is per plan)."""
+    cfgs = small_mix(8, 3, (800, 2000), 8)
+    plans = [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], n_aux=2, max_frames=8,
+                      weighting=w) for c, w in zip(cfgs, ["phat", "none", "none"])]
+    batch = srp.Batch(plans)
+    res = run_batch(batch, cfgs, [8, 8, 5])
+    for c, w, (m, a, p), l in zip(cfgs, ["phat", "none", "none"], res, [8, 8, 5]):
+        ref, _, _ = oracle.srp_map(c["Y"][:l], c["mic"], c["grid"], c["fs"], c["c"], c["K"],
+                                   mode="nyquist", n_aux=2, weighting=w)
+        check(m, a, p, ref, TOL["fp32"])
+    batch.close()

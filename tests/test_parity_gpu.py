@@ -387,3 +387,26 @@ def test_host_async_pipeline_matches_host_entry():
             assert np.array_equal(m, m1)
         assert np.array_equal(a, a1) and np.array_equal(p, p1)
     plan.close()
+
+
+@pytest.mark.parametrize("mode,precision", [("nyquist", "fp32"), ("conventional", "fp32"),
+                                            ("nyquist", "bf16")])
+def test_unweighted_cross_spectra_match_oracle(mode, precision):
+    """No GCC weighting (psi = y_m y_m'^*, Sec. 2.1): the whole path against
+    the oracle with the same weighting."""
+    cfg = synth.tiny_2d(seed=31, L=6)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], mode=mode,
+                    precision=precision, max_frames=6, weighting="none")
+    m, a, p = plan.map(dev(cfg["Y"]))
+    torch.cuda.synchronize()
+    maps = m.cpu().numpy()
+    ref, _, _ = oracle.srp_map(cfg["Y"], cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"],
+                               mode=mode, n_aux=2, weighting="none")
+    tol = TOL_FP32 if precision == "fp32" else TOL_HALF
+    if precision == "fp32":
+        check_against_oracle(maps, a.cpu().numpy(), ref, tol)
+    else:
+        pk = np.abs(ref).max(axis=1)
+        assert np.all(np.abs(maps - ref).max(axis=1) <= tol * pk)
+    check_self_consistent(maps, a.cpu().numpy(), p.cpu().numpy())
+    plan.close()
