@@ -315,17 +315,22 @@ def bench_ours(args):
 
     # reduced-precision variants of the same step (Nyquist, tensor cores)
     variants = {}
-    for prec in ("bf16", "fp16"):
+    for prec, resident in (("bf16", False), ("fp16", False), ("bf16", True)):
         pl = srp.Plan(mic, grid, w["fs"], 343.0, w["K"], mode="nyquist", n_aux=w["n_aux"],
-                      max_frames=L, precision=prec)
+                      max_frames=L, precision=prec, resident_weights=resident)
         srp.srp_set_timing(pl.handle, True)
         ms_v, st_v, _ = time_steps(make_step(pl), max(3, min(args.steps, 20)), args.warmup,
                                    flush, stream, world, stage_time(pl), name=f"room_3d_{prec}")
-        variants[prec] = {"ms_per_step": float(ms_v.mean()),
+        name = prec + ("_resident_weights" if resident else "")
+        variants[name] = {"ms_per_step": float(ms_v.mean()),
                           "value": world * J * Q * L / (float(ms_v.mean()) * 1e-3),
                           "map_ms": float(st_v.mean()),
                           "map_frac_of_bf16_peak": flops / (float(st_v.mean()) * 1e-3) / 1e12
                           / bf16_peak}
+        if resident:  # the map streams the interpolation matrix: report it against HBM
+            wb = float(pl.info.weight_bytes) + 4.0 * J * L
+            variants[name]["weight_bytes"] = int(pl.info.weight_bytes)
+            variants[name]["map_hbm_gbs"] = wb / (float(st_v.mean()) * 1e-3) / 1e9
         pl.close()
 
     conv_tc = bool(plans["conventional"].info.tensor_cores)

@@ -120,6 +120,12 @@ typedef struct {
     srp_weighting weighting;  /* GCC weighting of STFT input (ignored for cross spectra);
                                  SRP_WEIGHT_NONE is not available with SRP_PREC_FP16,
                                  whose range unnormalised spectra can exceed */
+    int32_t resident_weights; /* nonzero (Nyquist, tensor cores): precompute the sinc
+                                 interpolation matrix of Eq. SRPapprox once, at plan time,
+                                 keep it in device memory (J_pad x the used lag slots x
+                                 2 bytes, twice for FP32) and stream it into every map
+                                 instead of generating the weights on chip; the maps are
+                                 the same.  Batches generate the weights on chip */
 } srp_plan_desc;
 
 /* Sizes of a plan, computed on the host (no device needed). */
@@ -137,6 +143,7 @@ typedef struct {
                              accumulation bias (about 1.5e-8 per 16-element step) to
                              reach half the 1e-4 tolerance */
     size_t device_bytes;  /* bytes srp_plan allocates on the device */
+    size_t weight_bytes;  /* of which the resident interpolation matrix (0 if generated) */
 } srp_plan_info;
 
 typedef struct srp_plan_s *srp_handle;

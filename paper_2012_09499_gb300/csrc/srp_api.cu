@@ -139,6 +139,14 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         lay.n_chunks = (int)(sc / kLagPad);
         lay.N_tc = interp_tc_frames_per_cta(d->max_frames);
     }
+    if (d->resident_weights) {
+        if (!lay.tc || d->mode != SRP_MODE_NYQUIST)
+            return fail(SRP_ERR_UNSUPPORTED,
+                        "resident weights need a Nyquist plan on the tensor cores");
+        int64_t steps = 0;  // 16-slot MMA steps holding lags, per tile
+        for (int q = 0; q < lay.Q; ++q) steps += (tc_span(d, lay, q) + 15) / 16;
+        lay.tile_steps = (int)steps;
+    }
 
     // Fixed-point TDOA: the largest xf <= 24 with (max|x| + 2) 2^xf < 2^31.
     // Far-field directions must be unit vectors so that |x| <= d fs / c.
@@ -162,6 +170,8 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     lay.b_offc = lay.tc ? sizeof(int32_t) * lay.Q : 0;
     lay.b_xs = lay.tc ? sizeof(int2) * (size_t)lay.Q * (size_t)lay.J_pad : 0;
     lay.b_ctab = lay.tc ? sizeof(int4) * (size_t)lay.n_chunks : 0;
+    lay.b_w = lay.tile_steps ? (size_t)lay.n_tiles * lay.tile_steps * (half ? 1 : 2) * 4096 : 0;
+    lay.b_woff = lay.tile_steps ? sizeof(int32_t) * (size_t)lay.n_chunks : 0;
     lay.b_status = sizeof(int);
     lay.b_part = sizeof(unsigned long long) * (size_t)lay.L_pad * lay.n_tiles;
     if (d->host_io < 0 || d->host_io > 2) return fail(SRP_ERR_INVALID_ARG, "host_io must be 0, 1 or 2");
@@ -201,6 +211,7 @@ void fill_info(const Layout &lay, srp_plan_info *info) {
     info->max_frames = lay.L_max;
     info->tensor_cores = lay.tc ? 1 : 0;
     info->device_bytes = lay.total();
+    info->weight_bytes = lay.b_w;
 }
 
 template <typename T>
@@ -222,6 +233,8 @@ void release(srp_plan_s *h) {
     cudaFree(h->d_offc);
     cudaFree(h->d_xs);
     cudaFree(h->d_ctab);
+    cudaFree(h->d_w);
+    cudaFree(h->d_woff);
     cudaFree(h->d_status);
     cudaFree(h->d_part);
     cudaFree(h->d_in_stage);
@@ -341,6 +354,20 @@ srp_status build_tdoa(const srp_plan_desc *d, srp_plan_s *h) {
     }
     SRP_CUDA(cudaMemcpy(h->d_ctab, ctab.data(), lay.b_ctab, cudaMemcpyHostToDevice),
              "upload chunk table");
+    if (lay.tile_steps) {  // resident interpolation matrix: chunk offsets, then the weights
+        std::vector<int32_t> woff(lay.n_chunks);
+        int32_t at = 0;
+        for (int c = 0; c < lay.n_chunks; ++c) {
+            woff[c] = at;
+            at += ctab[c].w;
+        }
+        if (at != lay.tile_steps) return fail(SRP_ERR_UNSUPPORTED, "internal: step count");
+        SRP_CUDA(cudaMemcpy(h->d_woff, woff.data(), lay.b_woff, cudaMemcpyHostToDevice),
+                 "upload chunk offsets");
+        SRP_CUDA(launch_build_w(h->d_xs, h->d_ctab, h->d_woff, lay.n_chunks, lay.J_pad, lay.xf,
+                                lay.tile_steps, lay.n_tiles, h->precision, h->d_w, 0),
+                 "interpolation matrix kernel");
+    }
     return SRP_OK;
 }
 
@@ -392,7 +419,8 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
         SRP_CUDA(launch_interp_tc(h->xi_map, lay.N_tc, h->d_xs, h->d_ctab, lay.par1_used,
                                   lay.J_pad, lay.J, lay.Q, h->d_nq, lay.n_aux, lay.xf, lay.Sc,
                                   lay.L_pad, L, h->precision, h->mode == SRP_MODE_CONV ? 1 : 0,
-                                  lay.K, d_maps, h->d_part, lay.n_tiles, h->d_status, s),
+                                  lay.K, d_maps, h->d_part, lay.n_tiles, h->d_status, h->d_w,
+                                  h->d_woff, lay.tile_steps, s),
                  "tensor-core map kernel");
     } else if (h->mode == SRP_MODE_NYQUIST) {
         SRP_CUDA(launch_interp_simt(h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq, h->d_off, lay.n_aux,
@@ -489,6 +517,8 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     SRP_ALLOC(h->d_offc, L.b_offc);
     SRP_ALLOC(h->d_xs, L.b_xs);
     SRP_ALLOC(h->d_ctab, L.b_ctab);
+    SRP_ALLOC(h->d_w, L.b_w);
+    SRP_ALLOC(h->d_woff, L.b_woff);
     SRP_ALLOC(h->d_status, L.b_status);
     SRP_ALLOC(h->d_part, L.b_part);
     if (h->host_io) {

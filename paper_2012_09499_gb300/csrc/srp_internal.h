@@ -29,14 +29,15 @@ struct Layout {
     std::vector<int32_t> Nq, off, pm, pmp;  // per pair
     // tensor-core lag layout: pair q owns ceil(N'_q / 64) chunks of 64 slots
     int Sc = 0, n_chunks = 0, N_tc = 0, par1_used = 0;
+    int tile_steps = 0;  // resident interpolation matrix: 16-slot steps per tile (0: generated)
     bool tc = false;    // the Nyquist map runs on the tensor cores
     std::vector<int32_t> offc;
     // byte counts of every device buffer, in allocation order
-    size_t b_status = 0, b_offc = 0, b_xs = 0, b_ctab = 0;
+    size_t b_status = 0, b_offc = 0, b_xs = 0, b_ctab = 0, b_w = 0, b_woff = 0;
     size_t b_pairs = 0, b_nq = 0, b_off = 0, b_x = 0, b_twid = 0, b_psi = 0, b_xi = 0,
            b_xi16 = 0, b_part = 0, b_in_stage = 0, b_maps_stage = 0, b_small_stage = 0;
     size_t total() const {
-        return b_status + b_offc + b_xs + b_ctab + b_pairs + b_nq + b_off + b_x + b_twid + b_psi + b_xi + b_xi16 + b_part +
+        return b_status + b_offc + b_xs + b_ctab + b_w + b_woff + b_pairs + b_nq + b_off + b_x + b_twid + b_psi + b_xi + b_xi16 + b_part +
                b_in_stage + b_maps_stage + b_small_stage;
     }
 };
@@ -63,6 +64,8 @@ struct srp_plan_s {
     uint16_t *d_xi16 = nullptr;    // [1 or 2][L_pad][Sc] sign-folded GCC samples, 16-bit
     int32_t *d_offc = nullptr;     // [Q] first 16-bit lag slot of pair q (a multiple of 64)
     int2 *d_xs = nullptr;          // [Q][J_pad] (fixed-point TDOA, bits of (-1)^x0 sin(pi f)/pi)
+    void *d_w = nullptr;           // resident interpolation matrix (resident_weights plans)
+    int32_t *d_woff = nullptr;     // [n_chunks] first 16-slot step of each chunk in a tile
     int4 *d_ctab = nullptr;        // [n_chunks] (pair, bits of nmax - first slot, groups, MMA steps)
     int *d_status = nullptr;       // device error flags (bit 0: a bounded wait gave up)
     alignas(64) unsigned char xi_map[128] = {};  // CUtensorMap of d_xi16
@@ -136,7 +139,12 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
                              int par1_used, int64_t J_pad, int64_t J, int Q, const int32_t *nq,
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
                              int conv, int K, float *maps, unsigned long long *part, int n_tiles,
-                             int *status, cudaStream_t s);
+                             int *status, const void *w, const int32_t *woff, int tile_steps,
+                             cudaStream_t s);
+// Plan time: the resident interpolation matrix (operand A) of every tile.
+cudaError_t launch_build_w(const int2 *xs, const int4 *ctab, const int32_t *woff, int n_chunks,
+                           int64_t J_pad, int xf, int tile_steps, int n_tiles, int precision,
+                           void *w, cudaStream_t s);
 cudaError_t launch_conv_operand_tc(const float2 *psi, int L, int Q, int K, const int32_t *offc,
                                    uint16_t *b16, int L_pad, int S_pad, int fmt, cudaStream_t s);
 cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,

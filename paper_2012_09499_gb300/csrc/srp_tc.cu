@@ -135,13 +135,64 @@ struct TcArgs {
     int vec_maps;           // maps rows are 8-byte aligned (float2 stores)
     uint32_t a_col0;        // operand A in TMEM: first column of the A stages
     int par1_used;          // some chunk has two or more 16-lag steps
+    const uint4 *w;         // resident operand A (kW): the plan's interpolation matrix
+    const int32_t *woff;    // [n_chunks] first 16-slot step of chunk c within a tile's block
+    int tile_steps;         // 16-slot steps per 128-candidate tile
 };
+
+// ---------------------------------------------------------------------------
+// Plan time: the interpolation matrix (operand A) of a resident-weights plan.
+// For every 128-candidate tile t and chunk c, the sinc weights of the chunk's
+// nk used 16-slot steps, in the canonical K-major layout without swizzle (one
+// kAStep block per step: 16 groups of 8 rows, each two 128-byte core matrices
+// of 8 rows x 16 bytes along K), high parts then low parts for the FP32 split.
+// Chunk c of tile t starts (t * tile_steps + woff[c]) * hs * kAStep bytes in.
+// The weights are the generator's, so the maps equal those of on-chip
+// generation.
+// ---------------------------------------------------------------------------
+template <bool kSplit, bool kHalf>
+__global__ void __launch_bounds__(128) k_build_w(const int2 *__restrict__ xs,
+                                                 const int4 *__restrict__ ctab,
+                                                 const int32_t *__restrict__ woff, int n_chunks,
+                                                 int64_t J_pad, int xf, int tile_steps,
+                                                 uint4 *__restrict__ w) {
+    const int r = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * 128 + r;
+    const int hs = kSplit ? 2 : 1;
+    const uint32_t row_off = (uint32_t)((r >> 3) * 16 + (r & 7));  // uint4 units in a step
+    uint4 *tile = w + (size_t)blockIdx.x * tile_steps * hs * (kAStep / 16);
+    int q = -1;
+    float sp = 0.0f, f = 0.5f, x0f = 0.0f;
+    for (int c = 0; c < n_chunks; ++c) {
+        const int4 cur = ctab[c];
+        if (cur.x != q) {
+            q = cur.x;
+            const int2 e = xs[(size_t)q * J_pad + i];
+            int x0;
+            decode_tdoa(e.x, xf, x0, f);
+            if (f == 0.0f) f = 9.094947017729282e-13f;  // 2^-40, as in the plan
+            sp = __int_as_float(e.y);
+            x0f = (float)x0;
+        }
+        const float mc = x0f + __int_as_float(cur.y);
+        uint4 *hi = tile + (size_t)woff[c] * hs * (kAStep / 16);
+        uint4 *lo = hi + (size_t)cur.w * (kAStep / 16);
+        switch (cur.z) {
+            case 2: gen_groups<2, kSplit, kHalf, kAGlobal>(row_off, row_off, 0u, f, mc, sp, 0u, hi, lo); break;
+            case 4: gen_groups<4, kSplit, kHalf, kAGlobal>(row_off, row_off, 0u, f, mc, sp, 0u, hi, lo); break;
+            case 6: gen_groups<6, kSplit, kHalf, kAGlobal>(row_off, row_off, 0u, f, mc, sp, 0u, hi, lo); break;
+            default: gen_groups<8, kSplit, kHalf, kAGlobal>(row_off, row_off, 0u, f, mc, sp, 0u, hi, lo); break;
+        }
+    }
+}
 
 
 // kTm: operand A is generated into TMEM (32 columns per 64-slot stage and
 // part) and the MMAs read only B from shared memory; otherwise A is a
-// 128-byte-swizzled shared-memory tile like B.
-template <bool kSplit, bool kHalf, bool kConv, bool kTm>
+// 128-byte-swizzled shared-memory tile like B.  kW: A is not generated but
+// streamed from the plan's resident interpolation matrix by bulk copies (no
+// swizzle, one block per 16-slot step) next to B.
+template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false>
 __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
                                                            const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -180,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
-            mbar_init(full_bar(s), 128 + 1);
+            mbar_init(full_bar(s), kW ? 1 : 128 + 1);
             mbar_init(empty_bar(s), 2);
         }
         mbar_init(accum_bar, 2);
@@ -194,8 +245,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
     const uint32_t tmem = *tmem_slot;
 
     if (warp < 4) {
-        // ---------------- A generation: one candidate row per thread ----------------
         const int r = threadIdx.x;
+        if (!kW) {
+        // ---------------- A generation: one candidate row per thread ----------------
         const int64_t i = (int64_t)blockIdx.x * 128 + r;
         const uint32_t row = (uint32_t)r * 128u, sw = (uint32_t)(r & 7);
         // d = f + (m - e) for lag e of a group, where m = x0 + nmax - (first lag
@@ -287,6 +339,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             mbar_arrive(full_bar(st));
             cur = nxt;
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        }  // !kW
 
         // ---------------- epilogue: TMEM -> smem tile -> maps + argmax keys ----------------
         mbar_wait(accum_bar, 0, abort_flag, a.status);
@@ -363,7 +417,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                 if (c >= a.stages && !mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status))
                     break;
                 if (*abort_flag) break;
-                mbar_arrive_expect_tx(full_bar(st), bytes);
+                if (kW) {  // the chunk's used steps of the resident A, high then low parts
+                    const uint32_t a_bytes = (uint32_t)__ldg(&a.ctab[c]).w * kAStep;
+                    const uint4 *src = a.w + ((size_t)blockIdx.x * a.tile_steps + __ldg(&a.woff[c])) *
+                                                 (kSplit ? 2 : 1) * (kAStep / 16);
+                    mbar_arrive_expect_tx(full_bar(st), bytes + (kSplit ? 2u : 1u) * a_bytes);
+                    bulk_load(a_hi(st), src, a_bytes, full_bar(st));
+                    if (kSplit) bulk_load(a_lo(st), src + a_bytes / 16, a_bytes, full_bar(st));
+                } else {
+                    mbar_arrive_expect_tx(full_bar(st), bytes);
+                }
                 tma_load_2d(b_hi(st), &tmap, c * kChunk, l0, full_bar(st));
                 if (kSplit) tma_load_2d(b_lo(st), &tmap, c * kChunk, a.L_pad + l0, full_bar(st));
                 issued = c + 1;
@@ -405,6 +468,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                         if (kSplit) {
                             mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
                             mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
+                        }
+                    } else if (kW) {  // A blocks without swizzle, kAStep bytes per step
+                        const uint64_t wah = smem_desc_none(a_hi(st) + (uint32_t)kk * kAStep);
+                        const uint64_t wal = smem_desc_none(a_lo(st) + (uint32_t)kk * kAStep);
+                        mma_f16(dt, wah, dbh + adv, a.idesc, acc);
+                        if (kSplit) {
+                            mma_f16(dt, wah, dbl + adv, a.idesc, 1);
+                            mma_f16(dt, wal, dbh + adv, a.idesc, 1);
                         }
                     } else {
                         mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
@@ -452,18 +523,18 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-template <bool kSplit, bool kHalf, bool kConv, bool kTm>
+template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false>
 cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_t smem,
                       cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv, kTm>,
+        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv, kTm, kW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_interp_tc<kSplit, kHalf, kConv, kTm>
+    k_interp_tc<kSplit, kHalf, kConv, kTm, kW>
         <<<dim3((unsigned)a.n_tiles, grid_y), kThreads, smem, s>>>(map, a);
     return cudaGetLastError();
 }
@@ -528,9 +599,11 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
                              int par1_used, int64_t J_pad, int64_t J, int Q, const int32_t *nq,
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
                              int conv, int K, float *maps, unsigned long long *part, int n_tiles,
-                             int *status, cudaStream_t s) {
+                             int *status, const void *w, const int32_t *woff, int tile_steps,
+                             cudaStream_t s) {
     // N is the plan's frames per CTA: the height of the tensor map's box.
     if (L == 0) return cudaSuccess;
+    if (w != nullptr && conv) return cudaErrorInvalidValue;  // resident A: Nyquist only
     if (N < 16 || N > 256 || (N & 15)) return cudaErrorInvalidValue;
     const bool split = precision == SRP_PREC_FP32, half = precision == SRP_PREC_FP16;
     TcArgs a;
@@ -555,7 +628,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     const size_t tile_bytes = ((size_t)N * kMtStride * sizeof(float) + 1023) / 1024 * 1024;
     // Operand A in TMEM when two CTAs per SM keep 2N accumulator columns and at
     // least two A stages (32 columns per part) within 256 columns each.
-    const bool tm = 2 * N + 2 * hs * 32 <= 256;
+    const bool tm = w == nullptr && 2 * N + 2 * hs * 32 <= 256;
     int stages;
     size_t smem;
     if (tm) {
@@ -590,6 +663,9 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.par1_used = par1_used;
     a.K = K;
     a.vec_maps = (maps != nullptr && (J % 2) == 0 && (reinterpret_cast<uintptr_t>(maps) & 7) == 0);
+    a.w = static_cast<const uint4 *>(w);
+    a.woff = woff;
+    a.tile_steps = tile_steps;
     const int grid_y = (L + N - 1) / N;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(xi_map);
     if (conv) {
@@ -597,9 +673,27 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
         if (half) return launch_tc_a<false, true, true>(map, a, tm, grid_y, smem, s);
         return launch_tc_a<false, false, true>(map, a, tm, grid_y, smem, s);
     }
+    if (w != nullptr) {
+        if (split) return launch_tc<true, false, false, false, true>(map, a, grid_y, smem, s);
+        if (half) return launch_tc<false, true, false, false, true>(map, a, grid_y, smem, s);
+        return launch_tc<false, false, false, false, true>(map, a, grid_y, smem, s);
+    }
     if (split) return launch_tc_a<true, false, false>(map, a, tm, grid_y, smem, s);
     if (half) return launch_tc_a<false, true, false>(map, a, tm, grid_y, smem, s);
     return launch_tc_a<false, false, false>(map, a, tm, grid_y, smem, s);
+}
+
+cudaError_t launch_build_w(const int2 *xs, const int4 *ctab, const int32_t *woff, int n_chunks,
+                           int64_t J_pad, int xf, int tile_steps, int n_tiles, int precision,
+                           void *w, cudaStream_t s) {
+    uint4 *dst = static_cast<uint4 *>(w);
+    if (precision == SRP_PREC_FP32)
+        k_build_w<true, false><<<n_tiles, 128, 0, s>>>(xs, ctab, woff, n_chunks, J_pad, xf, tile_steps, dst);
+    else if (precision == SRP_PREC_FP16)
+        k_build_w<false, true><<<n_tiles, 128, 0, s>>>(xs, ctab, woff, n_chunks, J_pad, xf, tile_steps, dst);
+    else
+        k_build_w<false, false><<<n_tiles, 128, 0, s>>>(xs, ctab, woff, n_chunks, J_pad, xf, tile_steps, dst);
+    return cudaGetLastError();
 }
 
 }  // namespace srp

@@ -180,6 +180,25 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// Shared-memory matrix descriptor: K-major without swizzle, core matrices of
+// 8 rows x 16 bytes; LBO = 128 bytes between the two core matrices along K
+// of a 16-element step, SBO = 256 bytes between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc_none(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Bulk copy of bytes (a multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory, completing on the mbarrier with its byte count.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -247,22 +266,41 @@ __device__ __forceinline__ uint32_t pack_f16(float a, float b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// Where the weight generators put operand A.
+enum ADst : int {
+    kASmem = 0,    // shared-memory A tile, 128-byte swizzle
+    kATmem = 1,    // tensor memory
+    kAGlobal = 2   // global memory, canonical K-major layout without swizzle
+};
+constexpr uint32_t kAStep = 4096;  // one 16-slot MMA step of a 128-row A tile, 16-bit
+
 // Store group cc of a candidate row of operand A: 8 16-bit values hv (and,
-// with kSplit, their low parts lv).  kTm: into TMEM, four 32-bit columns per
-// group from column dst0 (dst1 for the low parts) of this thread's lane.
-// Otherwise into the shared-memory A tile with the 128-byte swizzle: row
-// address dst0, 16-byte chunk (cc0 + cc) ^ sw, low parts kATile bytes on.
-template <bool kSplit, bool kTm>
+// with kSplit, their low parts lv).
+//  kATmem: four 32-bit columns per group from column dst0 (dst1 for the low
+//    parts) of this thread's lane.
+//  kASmem: the A tile with the 128-byte swizzle: row address dst0, 16-byte
+//    chunk cc ^ sw, low parts kATile bytes on.
+//  kAGlobal: dst0 / dst1 index this row's first 16 bytes (as a uint4 offset
+//    within the step block) in the generic pointers g0 / g1: group cc is
+//    k-half cc & 1 of step cc >> 1, and a step block of kAStep bytes holds
+//    16 row groups of two k-halves of 8 rows x 16 bytes, so group cc lands
+//    (cc >> 1) * kAStep + (cc & 1) * 128 bytes past the row's position.
+template <bool kSplit, int kDst>
 __device__ __forceinline__ void store_group(uint32_t dst0, uint32_t dst1, uint32_t sw,
                                             uint32_t cc, const uint32_t (&hv)[4],
-                                            const uint32_t (&lv)[4]) {
-    if (kTm) {
+                                            const uint32_t (&lv)[4], uint4 *g0 = nullptr,
+                                            uint4 *g1 = nullptr) {
+    if (kDst == kATmem) {
         tmem_st4(dst0 + 4u * cc, hv[0], hv[1], hv[2], hv[3]);
         if (kSplit) tmem_st4(dst1 + 4u * cc, lv[0], lv[1], lv[2], lv[3]);
-    } else {
+    } else if (kDst == kASmem) {
         const uint32_t off = dst0 + ((cc ^ sw) << 4);
         st_shared_v4(off, hv[0], hv[1], hv[2], hv[3]);
         if (kSplit) st_shared_v4(off + kATile, lv[0], lv[1], lv[2], lv[3]);
+    } else {
+        const size_t at = (size_t)dst0 + (size_t)(cc >> 1) * (kAStep / 16) + (size_t)(cc & 1) * 8;
+        g0[at] = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        if (kSplit) g1[at] = make_uint4(lv[0], lv[1], lv[2], lv[3]);
     }
 }
 
@@ -270,9 +308,10 @@ __device__ __forceinline__ void store_group(uint32_t dst0, uint32_t dst1, uint32
 // w = sp / d with d = f + (mc - k) for lag slot k of the chunk, two lags per
 // reciprocal, stored by store_group (groups cc0 .. cc0 + NG - 1 of the row).
 // With kSplit, the low parts bf16(w - hi) are stored too.
-template <int NG, bool kSplit, bool kHalf, bool kTm>
+template <int NG, bool kSplit, bool kHalf, int kDst>
 __device__ __forceinline__ void gen_groups(uint32_t dst0, uint32_t dst1, uint32_t sw, float f,
-                                           float mc, float sp, uint32_t cc0 = 0) {
+                                           float mc, float sp, uint32_t cc0 = 0,
+                                           uint4 *g0 = nullptr, uint4 *g1 = nullptr) {
     const uint64_t f2 = pk2(f, f);
     const uint64_t two = pk2(2.0f, 2.0f);
     // m2 = (mc - k - 1, mc - k): the second lag of a pair first, so that
@@ -300,7 +339,7 @@ __device__ __forceinline__ void gen_groups(uint32_t dst0, uint32_t dst1, uint32_
                 }
             }
         }
-        store_group<kSplit, kTm>(dst0, dst1, sw, (uint32_t)cc + cc0, hv, lv);
+        store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv, lv, g0, g1);
     }
 }
 
@@ -308,9 +347,10 @@ __device__ __forceinline__ void gen_groups(uint32_t dst0, uint32_t dst1, uint32_
 // element pair (cos theta_k, -sin theta_k) of bins k0, k0 + 1, ..., i.e.
 // z = e^{-j theta_k}, starting from z0 and multiplied per bin by
 // w' = (p, q) = e^{-j 2 pi x / K}: z w' = (a p - b q, b p + a q) for z = (a, b).
-template <int NG, bool kSplit, bool kHalf, bool kTm>
+template <int NG, bool kSplit, bool kHalf, int kDst>
 __device__ __forceinline__ void gen_steer(uint32_t dst0, uint32_t dst1, uint32_t sw, float za,
-                                          float zb, float p, float q, uint32_t cc0 = 0) {
+                                          float zb, float p, float q, uint32_t cc0 = 0,
+                                          uint4 *g0 = nullptr, uint4 *g1 = nullptr) {
     uint64_t z = pk2(za, zb);
     const uint64_t pp = pk2(p, p), qq = pk2(-q, q);
 #pragma unroll
@@ -335,7 +375,7 @@ __device__ __forceinline__ void gen_steer(uint32_t dst0, uint32_t dst1, uint32_t
                 }
             }
         }
-        store_group<kSplit, kTm>(dst0, dst1, sw, (uint32_t)cc + cc0, hv, lv);
+        store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv, lv, g0, g1);
     }
 }
 

@@ -218,3 +218,26 @@ def test_footprint_counts_host_staging_slots():
         d, k = _desc(M=6, J=1000, K=512, max_frames=20, host_io=slots)
         stage = up(8 * 20 * 6 * 257) + up(4 * 20 * 1000) + 2 * up(4 * 32)
         assert srp.srp_plan_footprint(d) == base + slots * stage
+
+
+def test_resident_weights_footprint_and_limits():
+    """A resident interpolation matrix adds J_pad x (16-slot steps holding
+    lags) x 2 bytes (twice for FP32) and a chunk-offset table; it exists for
+    Nyquist tensor-core plans only."""
+    for prec, hs in (("fp32", 2), ("bf16", 1)):
+        d0, k0 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision=prec)
+        info, nq = srp.srp_plan_describe(d0)
+        d1, k1 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision=prec,
+                       resident_weights=True)
+        info1, _ = srp.srp_plan_describe(d1)
+        spans = 2 * nq + 5
+        steps = int(np.sum(-(-spans // 16)))
+        chunks = int(np.sum(-(-spans // 64)))
+        w = (1024 // 128) * steps * hs * 4096
+        assert info1.weight_bytes == w and info.weight_bytes == 0
+        assert srp.srp_plan_footprint(d1) == srp.srp_plan_footprint(d0) + w + 4 * chunks
+    for kw in (dict(mode="conventional"), dict(engine="cuda_cores")):
+        d, k = _desc(resident_weights=True, **kw)
+        with pytest.raises(srp.SrpError) as e:
+            srp.srp_plan_describe(d)
+        assert e.value.status == srp.SRP_ERR_UNSUPPORTED

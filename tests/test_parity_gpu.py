@@ -410,3 +410,26 @@ def test_unweighted_cross_spectra_match_oracle(mode, precision):
         assert np.all(np.abs(maps - ref).max(axis=1) <= tol * pk)
     check_self_consistent(maps, a.cpu().numpy(), p.cpu().numpy())
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+def test_resident_weights_equal_generated(precision):
+    """A plan that precomputes its interpolation matrix and streams it gives
+    bit-for-bit the maps of on-chip generation, and matches the oracle."""
+    cfg = synth.room_3d(seed=4, L=24, shape=(30, 24, 18), spacing=0.15)
+    maps = {}
+    for resident in (False, True):
+        plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], n_aux=2,
+                        precision=precision, max_frames=24, resident_weights=resident)
+        assert (plan.info.weight_bytes > 0) == resident
+        m, a, p = plan.map(dev(cfg["Y"]))
+        torch.cuda.synchronize()
+        srp.srp_poll_device_status(plan.handle)
+        maps[resident] = (m.cpu().numpy(), a.cpu().numpy())
+        plan.close()
+    assert np.array_equal(maps[True][0], maps[False][0])
+    assert np.array_equal(maps[True][1], maps[False][1])
+    ref = oracle_maps(cfg, "nyquist")
+    tol = TOL_FP32 if precision == "fp32" else TOL_HALF
+    pk = np.abs(ref).max(axis=1)
+    assert np.all(np.abs(maps[True][0] - ref).max(axis=1) <= tol * pk)
