@@ -319,9 +319,9 @@ def bench_ours(args):
         pl = srp.Plan(mic, grid, w["fs"], 343.0, w["K"], mode="nyquist", n_aux=w["n_aux"],
                       max_frames=L, precision=prec, resident_weights=resident)
         srp.srp_set_timing(pl.handle, True)
-        ms_v, st_v, _ = time_steps(make_step(pl), max(3, min(args.steps, 20)), args.warmup,
-                                   flush, stream, world, stage_time(pl), name=f"room_3d_{prec}")
         name = prec + ("_resident_weights" if resident else "")
+        ms_v, st_v, _ = time_steps(make_step(pl), max(3, min(args.steps, 20)), args.warmup,
+                                   flush, stream, world, stage_time(pl), name=f"room_3d_{name}")
         variants[name] = {"ms_per_step": float(ms_v.mean()),
                           "value": world * J * Q * L / (float(ms_v.mean()) * 1e-3),
                           "map_ms": float(st_v.mean()),
