@@ -629,9 +629,12 @@ def bench_serving(args):
     for name, mode, prec, dur in (("nyquist_bf16", "nyquist", "bf16", args.serve_seconds),
                                   ("conventional_fp32", "conventional", "fp32",
                                    min(args.serve_seconds, 1.0))):
+        # Nyquist streams keep their interpolation matrices resident (built once)
         plans = [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], mode=mode, n_aux=2,
-                          precision=prec, max_frames=BATCH_L) for c in cfgs]
+                          precision=prec, max_frames=BATCH_L,
+                          resident_weights=(mode == "nyquist")) for c in cfgs]
         res = serve_run(srp, plans, cfgs, SERVE_RATE, dur, 5)
+        res["resident_weight_bytes"] = int(sum(p.info.weight_bytes for p in plans))
         res["duration_s"] = dur
         res["tensor_core_streams"] = int(sum(p.info.tensor_cores for p in plans))
         out[name] = res

@@ -62,6 +62,9 @@ struct BatchInst {
     int64_t b_row0;           // first row of the plan's block of operand B
     int M, Q, K, n_aux, xf, n_chunks, n_tiles, par1_used, input_kind, Lb, max_frames;
     int weighting;            // srp_weighting of STFT input
+    const uint4 *w;           // resident interpolation matrix of the plan, or null
+    const int32_t *woff;      // [n_chunks] first 16-slot step of each chunk in a tile
+    int tile_steps;           // 16-slot steps per tile of w
     int pblocks;              // pair blocks of kPairBlock per frame
     int64_t op_row0;          // first block of the plan in the operand kernel's grid
     int64_t frame0;           // first block of the plan in the argmax kernel's grid
@@ -426,6 +429,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
             const BatchInst &I = a.inst[it.x];
             const int n_chunks = I.n_chunks, xf = I.xf;
             const int4 *ctab = I.ctab;
+            const bool resident = !kConv && !kTm && I.w != nullptr;  // A streamed, not generated
             int q = -1;
             float sp = 0.0f, f = 0.5f, x0f = 0.0f;
             int x0m = 0;
@@ -459,7 +463,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                 const uint32_t d0 = kTm ? tmem + lane_base + a_tm(st, 0) : a_hi(st) + row;
                 const uint32_t d1 = kTm ? tmem + lane_base + a_tm(st, 1) : 0u;
                 const int ng = cur.z;
-                if (kConv) {
+                if (resident) {
+                    // the TMA warp brings A; only the stage protocol below
+                } else if (kConv) {
                     const int k0 = cur.y;
                     const int rk = (int)(((long long)k0 * x0m) % K);
                     float sn, cs;
@@ -520,7 +526,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(full_bar(st), bytes);
+                    if (!kConv && !kTm && I.w != nullptr) {  // resident A: the chunk's used steps
+                        const int4 cc = __ldg(&I.ctab[c]);
+                        const uint32_t a_bytes = (uint32_t)cc.w * kAStep;
+                        const uint4 *src = I.w + ((size_t)it.y * I.tile_steps + __ldg(&I.woff[c])) *
+                                                     (kSplit ? 2 : 1) * (kAStep / 16);
+                        mbar_arrive_expect_tx(full_bar(st), bytes + (kSplit ? 2u : 1u) * a_bytes);
+                        bulk_load(a_hi(st), src, a_bytes, full_bar(st));
+                        if (kSplit) bulk_load(a_lo(st), src + a_bytes / 16, a_bytes, full_bar(st));
+                    } else {
+                        mbar_arrive_expect_tx(full_bar(st), bytes);
+                    }
                     const int y = (int)(r0 + (int64_t)c * (kSplit ? 2 : 1) * Lb);
                     tma_load_2d(b_hi(st), &tmap, 0, y, full_bar(st));
                     if (kSplit) tma_load_2d(b_lo(st), &tmap, 0, y + Lb, full_bar(st));
@@ -559,6 +575,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                 uint32_t acc = 0;  // the item's first MMA overwrites the accumulator
                 const int n_chunks = I.n_chunks;
                 const int4 *ctab = I.ctab;
+                const bool resident = !kConv && !kTm && I.w != nullptr;
                 for (int c = 0; c < n_chunks; ++c, ++g) {
                     const int st = g % a.stages;
                     const uint32_t ph = (uint32_t)(g / a.stages) & 1u;
@@ -579,6 +596,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                             if (kSplit) {
                                 mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
                                 mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
+                            }
+                        } else if (resident) {  // A blocks without swizzle, kAStep per step
+                            const uint64_t wah = smem_desc_none(a_hi(st) + (uint32_t)kk * kAStep);
+                            const uint64_t wal = smem_desc_none(a_lo(st) + (uint32_t)kk * kAStep);
+                            mma_f16(dt, wah, dbh + adv, a.idesc, acc);
+                            if (kSplit) {
+                                mma_f16(dt, wah, dbl + adv, a.idesc, 1);
+                                mma_f16(dt, wal, dbh + adv, a.idesc, 1);
                             }
                         } else {
                             mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
@@ -637,8 +662,9 @@ uint32_t persist_tmem_cols(const TileChoice &t, bool split) {
     return cols;
 }
 
-bool tile_fits(const TileChoice &t, bool split) {
+bool tile_fits(const TileChoice &t, bool split, bool any_resident) {
     if (t.N < 16 || t.N > 256 || (t.N & 15)) return false;
+    if (t.tm && any_resident) return false;  // streamed A blocks live in shared memory
     if (t.stages < 2 || t.stages > 4 || t.cps < 1 || t.cps > 2) return false;
     if (persist_tmem_cols(t, split) * (uint32_t)t.cps > 512u) return false;
     const size_t smem = persist_smem(t, split);
@@ -661,6 +687,7 @@ struct srp_batch_s {
     srp_precision precision = SRP_PREC_FP32;
     bool split = false, half = false;
     int max_L = 0, max_K = 0;
+    bool any_resident = false;  // some plan streams its interpolation matrix: A in shared memory
     TileChoice tiles;
     int n_ctas = 0, n_items = 0;
     int64_t op_blocks = 0, frame_blocks = 0, b_rows = 0;
@@ -994,6 +1021,10 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         I.par1_used = L.par1_used;
         I.input_kind = p->input_kind;
         I.weighting = p->weighting;
+        I.w = static_cast<const uint4 *>(p->d_w);
+        I.woff = p->d_woff;
+        I.tile_steps = L.tile_steps;
+        if (p->d_w != nullptr) b->any_resident = true;
         I.max_frames = L.L_max;
         I.pblocks = (L.Q + kPairBlock - 1) / kPairBlock;
         part += sizeof(unsigned long long) * (size_t)L.L_max * L.n_tiles;
@@ -1049,7 +1080,7 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
                 c.cps = cps;
                 c.stages = st;
                 c.tm = tm != 0;
-                if (tile_fits(c, b->split) && best.N == 0) best = c;
+                if (tile_fits(c, b->split, b->any_resident) && best.N == 0) best = c;
             }
         }
     }
@@ -1106,7 +1137,7 @@ srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const int32_t *L
                 c.stages = stg;
                 c.cps = cps;
                 c.tm = tm != 0;
-                if (!tile_fits(c, b->split)) continue;
+                if (!tile_fits(c, b->split, b->any_resident)) continue;
                 if ((result = batch_configure(b, c)) != SRP_OK) break;
                 float ms = 0.0f;
                 for (int rep = 0; rep < 3 && result == SRP_OK; ++rep) {

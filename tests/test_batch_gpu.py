@@ -228,3 +228,46 @@ def test_batch_mixes_weightings():
                                    mode="nyquist", n_aux=2, weighting=w)
         check(m, a, p, ref, TOL["fp32"])
     batch.close()
+
+
+def test_batch_far_field_and_cross_spectrum_input():
+    """Far-field direction grids and plans fed with ready cross spectra in one
+    batch, against the oracle."""
+    far = synth.paper_circle_setup(7, L=6, step_deg=6.0)
+    near = synth.uneven_instance(900, (900, 1500), 6, M=5, K=512)
+    psi = oracle.phat(near["Y"]).astype(np.complex64)
+    plans = [srp.Plan(far["mic"], far["grid"], far["fs"], far["c"], far["K"], n_aux=2,
+                      far_field=True, max_frames=6),
+             srp.Plan(near["mic"], near["grid"], near["fs"], near["c"], near["K"], n_aux=2,
+                      input_kind="cross", max_frames=6)]
+    batch = srp.Batch(plans)
+    d_in = [dev(far["Y"]), dev(psi)]
+    outs = batch.map(d_in, L=[6, 4])
+    torch.cuda.synchronize()
+    srp.srp_batch_poll_device_status(batch.handle)
+    ref_far, _, _ = oracle.srp_map(far["Y"], far["mic"], far["grid"], far["fs"], far["c"],
+                                   far["K"], mode="nyquist", n_aux=2, far_field=True)
+    ref_near, _, _ = oracle.srp_map(None, near["mic"], near["grid"], near["fs"], near["c"],
+                                    near["K"], mode="nyquist", n_aux=2, psi=psi[:4])
+    for (m, a, p), ref, l in zip(outs, [ref_far, ref_near], [6, 4]):
+        check(m.cpu().numpy(), a.cpu().numpy()[:l], p.cpu().numpy()[:l], ref, TOL["fp32"])
+    batch.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_batch_with_resident_weights(precision):
+    """Plans that stream their precomputed interpolation matrix, batched with
+    plans that generate it: the same maps as an all-generating batch."""
+    cfgs = small_mix(9, 4, (1500, 5000), 16)
+    gen = make_plans(cfgs, "nyquist", precision, 16)
+    mixed = [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], n_aux=2,
+                      precision=precision, max_frames=16, resident_weights=(k % 2 == 0))
+             for k, c in enumerate(cfgs)]
+    L = [16, 11, 16, 3]
+    b0, b1 = srp.Batch(gen), srp.Batch(mixed)
+    assert b1.info.tiles.operand_a == 2  # streamed A blocks live in shared memory
+    r0, r1 = run_batch(b0, cfgs, L), run_batch(b1, cfgs, L)
+    for (m0, a0, _), (m1, a1, _) in zip(r0, r1):
+        assert np.array_equal(m0, m1) and np.array_equal(a0, a1)
+    b0.close()
+    b1.close()

@@ -433,3 +433,17 @@ def test_resident_weights_equal_generated(precision):
     tol = TOL_FP32 if precision == "fp32" else TOL_HALF
     pk = np.abs(ref).max(axis=1)
     assert np.all(np.abs(maps[True][0] - ref).max(axis=1) <= tol * pk)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_half_precision_wide_frame_tile(precision):
+    """150 frames (a 160-frame tile per CTA): operand A stays in shared memory,
+    because two CTAs per SM cannot hold 2 x 160 accumulator columns plus A
+    stages in tensor memory."""
+    cfg = synth.tiny_2d(seed=41, L=150)
+    maps, idx, peak = gpu_run(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], cfg["Y"],
+                              "nyquist", 2, precision=precision)
+    ref = oracle_maps(cfg, "nyquist")
+    pk = np.abs(ref).max(axis=1)
+    assert np.all(np.abs(maps - ref).max(axis=1) <= TOL_HALF * pk)
+    check_self_consistent(maps, idx, peak)
