@@ -63,7 +63,7 @@ typedef enum {
     SRP_ERR_INVALID_ARG = 1, /* an argument is out of range or NULL */
     SRP_ERR_OOM = 2,         /* a device or host allocation failed */
     SRP_ERR_CUDA = 3,        /* a CUDA call failed (see srp_last_error_message) */
-    SRP_ERR_UNSUPPORTED = 4, /* valid request this build does not implement */
+    SRP_ERR_UNSUPPORTED = 4, /* valid request the library does not implement */
     SRP_ERR_TIMEOUT = 5      /* a bounded device wait gave up */
 } srp_status;
 
