@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *gbase = smem_raw + (base - raw);
-    // full[4], empty[4], acc_full[2], acc_empty[2], drain
+    // full[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2], drain
     uint64_t *bars = reinterpret_cast<uint64_t *>(gbase);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + 128);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + 132);
@@ -265,10 +265,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                                           (uint32_t)kXRing * 128u * 8u);
 
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
-    auto empty_bar = [&](int s) { return smem_u32(&bars[4 + s]); };
-    auto acc_full = [&](int b) { return smem_u32(&bars[8 + b]); };
-    auto acc_empty = [&](int b) { return smem_u32(&bars[10 + b]); };
-    const uint32_t drain = smem_u32(&bars[12]);
+    auto empty_bar = [&](int s) { return smem_u32(&bars[kMaxStages + s]); };
+    auto acc_full = [&](int b) { return smem_u32(&bars[2 * kMaxStages + b]); };
+    auto acc_empty = [&](int b) { return smem_u32(&bars[2 * kMaxStages + 2 + b]); };
+    const uint32_t drain = smem_u32(&bars[2 * kMaxStages + 4]);
+    static_assert((2 * kMaxStages + 5) * 8 <= 128, "barrier block overlaps the TMEM slot");
     auto a_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes; };
     auto a_lo = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + kATile; };
     auto b_hi = [&](int s) {
@@ -665,7 +666,7 @@ uint32_t persist_tmem_cols(const TileChoice &t, bool split) {
 bool tile_fits(const TileChoice &t, bool split, bool any_resident) {
     if (t.N < 16 || t.N > 256 || (t.N & 15)) return false;
     if (t.tm && any_resident) return false;  // streamed A blocks live in shared memory
-    if (t.stages < 2 || t.stages > 4 || t.cps < 1 || t.cps > 2) return false;
+    if (t.stages < 2 || t.stages > kMaxStages || t.cps < 1 || t.cps > 2) return false;
     if (persist_tmem_cols(t, split) * (uint32_t)t.cps > 512u) return false;
     const size_t smem = persist_smem(t, split);
     if (smem > (size_t)kMaxSmemCta) return false;

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *gbase = smem_raw + (base - raw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase);  // full[4], empty[4], accum
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase);  // full[kMaxStages], empty[kMaxStages], accum
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + 80);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + 84);
     const uint32_t b_tile = (uint32_t)a.N * 128u;
@@ -213,8 +213,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
     float *mt = reinterpret_cast<float *>(gbase + 1024u);
 
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
-    auto empty_bar = [&](int s) { return smem_u32(&bars[4 + s]); };
-    const uint32_t accum_bar = smem_u32(&bars[8]);
+    auto empty_bar = [&](int s) { return smem_u32(&bars[kMaxStages + s]); };
+    const uint32_t accum_bar = smem_u32(&bars[2 * kMaxStages]);
     auto a_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes; };
     auto a_lo = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + kATile; };
     auto b_hi = [&](int s) {
@@ -655,6 +655,8 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
         if (stages < 2 || stages * stage < tile_bytes) return cudaErrorInvalidConfiguration;
         smem = fixed + stage * (size_t)stages;
     }
+    // the barrier block holds kMaxStages full and empty barriers
+    if (stages < 2 || stages > kMaxStages) return cudaErrorInvalidConfiguration;
     a.stages = stages;
     a.maps = maps;
     a.part = part;

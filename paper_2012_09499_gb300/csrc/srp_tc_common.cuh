@@ -23,6 +23,7 @@ constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
 constexpr int kXRing = 8;            // (TDOA, sp) prefetch ring (slots per candidate row)
 constexpr int kXAhead = kXRing - 1;  // pairs in flight ahead of the current one
 constexpr int kMtStride = 130;       // floats per frame row of the epilogue tile
+constexpr int kMaxStages = 4;        // pipeline stages the kernels' barrier blocks hold
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
