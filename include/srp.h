@@ -120,12 +120,14 @@ typedef struct {
     srp_weighting weighting;  /* GCC weighting of STFT input (ignored for cross spectra);
                                  SRP_WEIGHT_NONE is not available with SRP_PREC_FP16,
                                  whose range unnormalised spectra can exceed */
-    int32_t resident_weights; /* nonzero (Nyquist, tensor cores): precompute the sinc
-                                 interpolation matrix of Eq. SRPapprox once, at plan time,
-                                 keep it in device memory (J_pad x the used lag slots x
-                                 2 bytes, twice for FP32) and stream it into every map
-                                 instead of generating the weights on chip; the maps are
-                                 the same.  Batches generate the weights on chip */
+    float resident_fraction;  /* in [0, 1] (Nyquist, tensor cores): the part of the sinc
+                                 interpolation matrix of Eq. SRPapprox (counted in 16-lag
+                                 steps, whole pairs, interleaved with the others) that is
+                                 computed once, at plan time, kept in device memory
+                                 (J_pad x its lag slots x 2 bytes, twice for FP32) and
+                                 streamed into every map; the rest is generated on chip
+                                 while it streams.  0: all generated; 1: all streamed.
+                                 The maps are the same either way */
 } srp_plan_desc;
 
 /* Sizes of a plan, computed on the host (no device needed). */

@@ -139,13 +139,27 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         lay.n_chunks = (int)(sc / kLagPad);
         lay.N_tc = interp_tc_frames_per_cta(d->max_frames);
     }
-    if (d->resident_weights) {
+    if (!(d->resident_fraction >= 0.0f && d->resident_fraction <= 1.0f))
+        return fail(SRP_ERR_INVALID_ARG, "resident_fraction must be in [0, 1]");
+    if (d->resident_fraction > 0.0f) {
         if (!lay.tc || d->mode != SRP_MODE_NYQUIST)
             return fail(SRP_ERR_UNSUPPORTED,
                         "resident weights need a Nyquist plan on the tensor cores");
-        int64_t steps = 0;  // 16-slot MMA steps holding lags, per tile
-        for (int q = 0; q < lay.Q; ++q) steps += (tc_span(d, lay, q) + 15) / 16;
-        lay.tile_steps = (int)steps;
+        // whole pairs, interleaved: pair q is streamed when that brings the
+        // streamed steps closer to the fraction of the steps so far
+        const double frac = d->resident_fraction;
+        int64_t total = 0, streamed = 0;
+        lay.streamed.assign(lay.Q, 0);
+        for (int q = 0; q < lay.Q; ++q) {
+            const int64_t s_q = (tc_span(d, lay, q) + 15) / 16;  // 16-slot MMA steps of pair q
+            total += s_q;
+            const double target = frac * (double)total;
+            if (fabs((double)(streamed + s_q) - target) < fabs((double)streamed - target)) {
+                lay.streamed[q] = 1;
+                streamed += s_q;
+            }
+        }
+        lay.tile_steps = (int)streamed;
     }
 
     // Fixed-point TDOA: the largest xf <= 24 with (max|x| + 2) 2^xf < 2^31.
@@ -355,11 +369,11 @@ srp_status build_tdoa(const srp_plan_desc *d, srp_plan_s *h) {
     SRP_CUDA(cudaMemcpy(h->d_ctab, ctab.data(), lay.b_ctab, cudaMemcpyHostToDevice),
              "upload chunk table");
     if (lay.tile_steps) {  // resident interpolation matrix: chunk offsets, then the weights
-        std::vector<int32_t> woff(lay.n_chunks);
+        std::vector<int32_t> woff(lay.n_chunks);  // -1: the chunk's weights are generated
         int32_t at = 0;
         for (int c = 0; c < lay.n_chunks; ++c) {
-            woff[c] = at;
-            at += ctab[c].w;
+            woff[c] = lay.streamed[ctab[c].x] ? at : -1;
+            if (woff[c] >= 0) at += ctab[c].w;
         }
         if (at != lay.tile_steps) return fail(SRP_ERR_UNSUPPORTED, "internal: step count");
         SRP_CUDA(cudaMemcpy(h->d_woff, woff.data(), lay.b_woff, cudaMemcpyHostToDevice),

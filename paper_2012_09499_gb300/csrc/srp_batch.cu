@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
             const BatchInst &I = a.inst[it.x];
             const int n_chunks = I.n_chunks, xf = I.xf;
             const int4 *ctab = I.ctab;
-            const bool resident = !kConv && !kTm && I.w != nullptr;  // A streamed, not generated
+            const bool resident = !kConv && !kTm && I.w != nullptr;  // some chunks streamed
             int q = -1;
             float sp = 0.0f, f = 0.5f, x0f = 0.0f;
             int x0m = 0;
@@ -464,8 +464,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                 const uint32_t d0 = kTm ? tmem + lane_base + a_tm(st, 0) : a_hi(st) + row;
                 const uint32_t d1 = kTm ? tmem + lane_base + a_tm(st, 1) : 0u;
                 const int ng = cur.z;
-                if (resident) {
-                    // the TMA warp brings A; only the stage protocol below
+                if (resident && __ldg(&I.woff[c]) >= 0) {
+                    // the TMA warp brings this chunk's A; only the stage protocol below
                 } else if (kConv) {
                     const int k0 = cur.y;
                     const int rk = (int)(((long long)k0 * x0m) % K);
@@ -527,10 +527,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                         ok = false;
                         break;
                     }
-                    if (!kConv && !kTm && I.w != nullptr) {  // resident A: the chunk's used steps
+                    const int wo = (!kConv && !kTm && I.w != nullptr) ? __ldg(&I.woff[c]) : -1;
+                    if (wo >= 0) {  // resident A: the chunk's used steps
                         const int4 cc = __ldg(&I.ctab[c]);
                         const uint32_t a_bytes = (uint32_t)cc.w * kAStep;
-                        const uint4 *src = I.w + ((size_t)it.y * I.tile_steps + __ldg(&I.woff[c])) *
+                        const uint4 *src = I.w + ((size_t)it.y * I.tile_steps + wo) *
                                                      (kSplit ? 2 : 1) * (kAStep / 16);
                         mbar_arrive_expect_tx(full_bar(st), bytes + (kSplit ? 2u : 1u) * a_bytes);
                         bulk_load(a_hi(st), src, a_bytes, full_bar(st));
@@ -589,6 +590,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                     const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
                     const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
                     const int nk = __ldg(&ctab[c]).w;
+                    const bool streamed = resident && __ldg(&I.woff[c]) >= 0;
                     for (int kk = par; kk < nk; kk += 2) {
                         const uint64_t adv = (uint64_t)(kk * 2);
                         const uint32_t ac = (uint32_t)(kk * 8);
@@ -598,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                                 mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
                                 mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
                             }
-                        } else if (resident) {  // A blocks without swizzle, kAStep per step
+                        } else if (streamed) {  // A blocks without swizzle, kAStep per step
                             const uint64_t wah = smem_desc_none(a_hi(st) + (uint32_t)kk * kAStep);
                             const uint64_t wal = smem_desc_none(a_lo(st) + (uint32_t)kk * kAStep);
                             mma_f16(dt, wah, dbh + adv, a.idesc, acc);

@@ -30,6 +30,7 @@ struct Layout {
     // tensor-core lag layout: pair q owns ceil(N'_q / 64) chunks of 64 slots
     int Sc = 0, n_chunks = 0, N_tc = 0, par1_used = 0;
     int tile_steps = 0;  // resident interpolation matrix: 16-slot steps per tile (0: generated)
+    std::vector<char> streamed;  // per pair: its weights are resident and streamed
     bool tc = false;    // the Nyquist map runs on the tensor cores
     std::vector<int32_t> offc;
     // byte counts of every device buffer, in allocation order

@@ -174,8 +174,10 @@ __global__ void __launch_bounds__(128) k_build_w(const int2 *__restrict__ xs,
             sp = __int_as_float(e.y);
             x0f = (float)x0;
         }
+        const int wo = woff[c];
+        if (wo < 0) continue;  // generated on chip by the map kernel
         const float mc = x0f + __int_as_float(cur.y);
-        uint4 *hi = tile + (size_t)woff[c] * hs * (kAStep / 16);
+        uint4 *hi = tile + (size_t)wo * hs * (kAStep / 16);
         uint4 *lo = hi + (size_t)cur.w * (kAStep / 16);
         switch (cur.z) {
             case 2: gen_groups<2, kSplit, kHalf, kAGlobal>(row_off, row_off, 0u, f, mc, sp, 0u, hi, lo); break;
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
-            mbar_init(full_bar(s), kW ? 1 : 128 + 1);
+            mbar_init(full_bar(s), 128 + 1);
             mbar_init(empty_bar(s), 2);
         }
         mbar_init(accum_bar, 2);
@@ -246,8 +248,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
 
     if (warp < 4) {
         const int r = threadIdx.x;
-        if (!kW) {
+        {
         // ---------------- A generation: one candidate row per thread ----------------
+        // (kW: chunks whose weights are resident are streamed by the TMA warp and
+        // only pass through the stage barriers here)
         const int64_t i = (int64_t)blockIdx.x * 128 + r;
         const uint32_t row = (uint32_t)r * 128u, sw = (uint32_t)(r & 7);
         // d = f + (m - e) for lag e of a group, where m = x0 + nmax - (first lag
@@ -310,7 +314,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
             const uint32_t d0 = kTm ? tmem + lane_base + a_tm(st, 0) : a_hi(st) + row;
             const uint32_t d1 = kTm ? tmem + lane_base + a_tm(st, 1) : 0u;
-            if (kConv) {
+            if (kW && __ldg(&a.woff[c]) >= 0) {
+                // resident: the TMA warp brings this chunk's weights
+            } else if (kConv) {
                 // exact seed e^{-j theta_k0} for the chunk's first bin k0 = cur.y
                 const int k0 = cur.y;
                 const int rk = (int)(((long long)k0 * x0m) % a.K);
@@ -340,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             cur = nxt;
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
-        }  // !kW
+        }
 
         // ---------------- epilogue: TMEM -> smem tile -> maps + argmax keys ----------------
         mbar_wait(accum_bar, 0, abort_flag, a.status);
@@ -417,9 +423,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                 if (c >= a.stages && !mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status))
                     break;
                 if (*abort_flag) break;
-                if (kW) {  // the chunk's used steps of the resident A, high then low parts
+                const int wo = kW ? __ldg(&a.woff[c]) : -1;
+                if (wo >= 0) {  // the chunk's used steps of the resident A, high then low parts
                     const uint32_t a_bytes = (uint32_t)__ldg(&a.ctab[c]).w * kAStep;
-                    const uint4 *src = a.w + ((size_t)blockIdx.x * a.tile_steps + __ldg(&a.woff[c])) *
+                    const uint4 *src = a.w + ((size_t)blockIdx.x * a.tile_steps + wo) *
                                                  (kSplit ? 2 : 1) * (kAStep / 16);
                     mbar_arrive_expect_tx(full_bar(st), bytes + (kSplit ? 2u : 1u) * a_bytes);
                     bulk_load(a_hi(st), src, a_bytes, full_bar(st));
@@ -460,6 +467,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                 const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
                 const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
                 const int nk = __ldg(&a.ctab[c]).w;  // 16-lag steps holding lags of the pair
+                const bool streamed = kW && __ldg(&a.woff[c]) >= 0;
                 for (int kk = par; kk < nk; kk += 2) {
                     const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
                     const uint32_t ac = (uint32_t)(kk * 8);   // 16 values in 8 TMEM columns
@@ -469,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                             mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
                             mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
                         }
-                    } else if (kW) {  // A blocks without swizzle, kAStep bytes per step
+                    } else if (streamed) {  // A blocks without swizzle, kAStep bytes per step
                         const uint64_t wah = smem_desc_none(a_hi(st) + (uint32_t)kk * kAStep);
                         const uint64_t wal = smem_desc_none(a_lo(st) + (uint32_t)kk * kAStep);
                         mma_f16(dt, wah, dbh + adv, a.idesc, acc);

@@ -40,7 +40,7 @@ class srp_plan_desc(ctypes.Structure):
         ("mode", ctypes.c_int), ("n_aux", ctypes.c_int32), ("precision", ctypes.c_int),
         ("input_kind", ctypes.c_int), ("max_frames", ctypes.c_int32),
         ("host_io", ctypes.c_int32), ("engine", ctypes.c_int), ("weighting", ctypes.c_int),
-        ("resident_weights", ctypes.c_int32),
+        ("resident_fraction", ctypes.c_float),
     ]
 
 
@@ -180,7 +180,7 @@ def _stream(s):
 
 def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="fp32",
               input_kind="stft", max_frames=64, far_field=False, host_io=False, engine="auto",
-              weighting="phat", resident_weights=False):
+              weighting="phat", resident_weights=False, resident_fraction=None):
     """Fill an srp_plan_desc; returns (desc, keep-alive arrays)."""
     mic = np.ascontiguousarray(mic_xyz, np.float64)
     grid = np.ascontiguousarray(grid_xyz, np.float64)
@@ -199,7 +199,9 @@ def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="f
     d.host_io = int(host_io)  # 0, 1 (srp_map_host) or 2 (also srp_map_host_async)
     d.engine = ENGINES[engine]
     d.weighting = WEIGHTINGS[weighting]
-    d.resident_weights = 1 if resident_weights else 0
+    # resident_weights=True streams the whole matrix; resident_fraction a part of it
+    d.resident_fraction = float(resident_fraction if resident_fraction is not None
+                                else (1.0 if resident_weights else 0.0))
     return d, (mic, grid)
 
 

@@ -241,3 +241,18 @@ def test_resident_weights_footprint_and_limits():
         with pytest.raises(srp.SrpError) as e:
             srp.srp_plan_describe(d)
         assert e.value.status == srp.SRP_ERR_UNSUPPORTED
+
+
+def test_partial_resident_fraction():
+    """A resident fraction keeps whole pairs' weights, about that fraction of
+    the 16-slot steps; out-of-range fractions are refused."""
+    d1, k1 = _desc(M=8, J=1000, K=1024, n_aux=2, precision="bf16", resident_fraction=1.0)
+    dh, kh = _desc(M=8, J=1000, K=1024, n_aux=2, precision="bf16", resident_fraction=0.5)
+    full = srp.srp_plan_describe(d1)[0].weight_bytes
+    half = srp.srp_plan_describe(dh)[0].weight_bytes
+    assert 0.3 * full < half < 0.7 * full
+    for bad in (-0.1, 1.5, float("nan")):
+        d, k = _desc(resident_fraction=bad)
+        with pytest.raises(srp.SrpError) as e:
+            srp.srp_plan_describe(d)
+        assert e.value.status == srp.SRP_ERR_INVALID_ARG

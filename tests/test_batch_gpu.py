@@ -261,7 +261,7 @@ def test_batch_with_resident_weights(precision):
     cfgs = small_mix(9, 4, (1500, 5000), 16)
     gen = make_plans(cfgs, "nyquist", precision, 16)
     mixed = [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], n_aux=2,
-                      precision=precision, max_frames=16, resident_weights=(k % 2 == 0))
+                      precision=precision, max_frames=16, resident_fraction=[1.0, 0.0, 0.5, 0.3][k])
              for k, c in enumerate(cfgs)]
     L = [16, 11, 16, 3]
     b0, b1 = srp.Batch(gen), srp.Batch(mixed)

@@ -414,25 +414,27 @@ def test_unweighted_cross_spectra_match_oracle(mode, precision):
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_resident_weights_equal_generated(precision):
-    """A plan that precomputes its interpolation matrix and streams it gives
-    bit-for-bit the maps of on-chip generation, and matches the oracle."""
+    """A plan that precomputes all or part of its interpolation matrix and
+    streams it (generating the rest) gives bit-for-bit the maps of on-chip
+    generation, and matches the oracle."""
     cfg = synth.room_3d(seed=4, L=24, shape=(30, 24, 18), spacing=0.15)
     maps = {}
-    for resident in (False, True):
+    for frac in (0.0, 1.0, 0.5, 0.3):
         plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], n_aux=2,
-                        precision=precision, max_frames=24, resident_weights=resident)
-        assert (plan.info.weight_bytes > 0) == resident
+                        precision=precision, max_frames=24, resident_fraction=frac)
+        assert (plan.info.weight_bytes > 0) == (frac > 0)
         m, a, p = plan.map(dev(cfg["Y"]))
         torch.cuda.synchronize()
         srp.srp_poll_device_status(plan.handle)
-        maps[resident] = (m.cpu().numpy(), a.cpu().numpy())
+        maps[frac] = (m.cpu().numpy(), a.cpu().numpy())
         plan.close()
-    assert np.array_equal(maps[True][0], maps[False][0])
-    assert np.array_equal(maps[True][1], maps[False][1])
+    for frac in (1.0, 0.5, 0.3):
+        assert np.array_equal(maps[frac][0], maps[0.0][0]), frac
+        assert np.array_equal(maps[frac][1], maps[0.0][1]), frac
     ref = oracle_maps(cfg, "nyquist")
     tol = TOL_FP32 if precision == "fp32" else TOL_HALF
     pk = np.abs(ref).max(axis=1)
-    assert np.all(np.abs(maps[True][0] - ref).max(axis=1) <= tol * pk)
+    assert np.all(np.abs(maps[0.5][0] - ref).max(axis=1) <= tol * pk)
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
