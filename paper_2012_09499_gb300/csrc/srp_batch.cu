@@ -170,14 +170,37 @@ __global__ void __launch_bounds__(128) k_batch_operands(const BatchInst *__restr
         }
         return;
     }
-    // Nyquist: a_k psi of every pair of the block, then its critical samples
+    // Nyquist: a_k psi of every pair of the block, then its critical samples.
+    // The loads of a bin for all the block's pairs are issued before any
+    // arithmetic, so that their latencies overlap.
     for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = I.twid[j];
-    for (int j = 0; j < np; ++j)
-        for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
-            const float2 v = cross(j, k);
-            const float a = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
-            ps[j * Kb + k] = make_float2(a * v.x, a * v.y);
+    const bool stft = I.input_kind == SRP_IN_STFT;
+    for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
+        float2 u[kPairBlock], v[kPairBlock];
+#pragma unroll
+        for (int j = 0; j < kPairBlock; ++j) {
+            if (j < np) {
+                if (stft) {
+                    const int2 pr = I.pairs[q0 + j];
+                    u[j] = in[((size_t)l * I.M + pr.x) * Kb + k];
+                    v[j] = in[((size_t)l * I.M + pr.y) * Kb + k];
+                } else {
+                    u[j] = in[((size_t)l * Q + q0 + j) * Kb + k];
+                }
+            }
         }
+        const float a = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
+#pragma unroll
+        for (int j = 0; j < kPairBlock; ++j) {
+            if (j < np) {
+                float2 c = u[j];
+                if (stft)
+                    c = I.weighting == SRP_WEIGHT_NONE ? times_conj(u[j], v[j])
+                                                       : times_conj(unit_phase(u[j]), unit_phase(v[j]));
+                ps[j * Kb + k] = make_float2(a * c.x, a * c.y);
+            }
+        }
+    }
     __syncthreads();
     gcc_rows(tw, ps, Kb, np, K, [&](int j) { return I.nq[q0 + j] + I.n_aux; },
              [&](int j, int t, int nl, float v) {
