@@ -194,6 +194,16 @@ def time_steps(step, steps, warmup, flush, stream, world, timed_stage=None, name
     return ms, np.array(stage_ms), wall
 
 
+def measured_hbm_peak():
+    """HBM copy bandwidth (GB/s) measured on this machine, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
 def measured_bf16_peak():
     """Dense BF16 TFLOP/s measured on this machine (burst), else the fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -436,9 +446,13 @@ def bench_batched(args, flush, stream):
            "arrays": n_arrays, "frames_per_array": BATCH_L, "sum_J": int(Js.sum()),
            "mean_pairs": float(Qs.mean()), "l2": "flushed between timed steps (256 MB write)"}
     L = [BATCH_L] * n_arrays
-    for prec in ("fp32", "bf16"):
+    # FP32 and BF16 generating the sinc weights on chip; BF16 again with every
+    # array's interpolation matrix resident in HBM and streamed
+    for name, prec, resident in (("fp32", "fp32", False), ("bf16", "bf16", False),
+                                 ("bf16_resident_weights", "bf16", True)):
         plans = [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], mode="nyquist", n_aux=2,
-                          precision=prec, max_frames=BATCH_L) for c in cfgs]
+                          precision=prec, max_frames=BATCH_L, resident_weights=resident)
+                 for c in cfgs]
         S = np.array([p.info.S for p in plans], np.float64)
         flops = float((2.0 * Js * S * BATCH_L).sum())
         batch = srp.Batch(plans)
@@ -450,7 +464,7 @@ def bench_batched(args, flush, stream):
             srp.srp_map_batch(batch.handle, d_in, L, maps, ams, pks, stream)
 
         steps = max(3, min(args.steps, args.batch_steps))
-        ms, _, _ = time_steps(step, steps, args.warmup, flush, stream, 1, name=f"batched_{prec}")
+        ms, _, _ = time_steps(step, steps, args.warmup, flush, stream, 1, name=f"batched_{name}")
         srp.srp_batch_set_timing(batch.handle, True)
         st = []
         for k in range(3):
@@ -464,7 +478,8 @@ def bench_batched(args, flush, stream):
         info = batch.info
         peak = bf16_peak / 3.0 if prec == "fp32" else bf16_peak
         achieved = flops / (stage["map"] * 1e-3) / 1e12
-        out[prec] = {
+        wbytes = float(sum(p.info.weight_bytes for p in plans))
+        out[name] = {
             "value": cells / (float(ms.mean()) * 1e-3), "unit": UNIT,
             "ms_per_step": float(ms.mean()), "steps": steps,
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
@@ -473,12 +488,23 @@ def bench_batched(args, flush, stream):
                       "stages": info.tiles.stages, "ctas_per_sm": info.tiles.ctas_per_sm,
                       "tuned_ms": float(info.tuned_ms)},
             "work_items": int(info.items), "persistent_ctas": int(info.ctas),
-            "roofline": {"kernel": "k_map_batch_tc (persistent, on-chip sinc weights)",
-                         "bound": "tensor", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak,
-                         "algorithmic": f"sum 2*J*S*L = {flops:.4g} flop per launch",
-                         "peak_source": f"measured bf16 {bf16_peak:.1f} TFLOP/s ({peak_src})"
-                                        + (" / 3 products" if prec == "fp32" else "")},
+            "resident_weight_bytes": int(sum(p.info.weight_bytes for p in plans)),
+            "roofline": ({"kernel": "k_map_batch_tc (persistent, streamed resident weights)",
+                          "bound": "hbm",
+                          "achieved": (wbytes + 4.0 * Js.sum() * BATCH_L) / (stage["map"] * 1e-3) / 1e9,
+                          "peak": measured_hbm_peak()[0], "unit": "GB/s",
+                          "frac": (wbytes + 4.0 * Js.sum() * BATCH_L) / (stage["map"] * 1e-3) / 1e9
+                                  / measured_hbm_peak()[0],
+                          "algorithmic": f"resident weights {wbytes:.4g} B + maps "
+                                         f"{4.0 * Js.sum() * BATCH_L:.4g} B per launch",
+                          "peak_source": f"measured HBM copy ({measured_hbm_peak()[1]})"}
+                         if resident else
+                         {"kernel": "k_map_batch_tc (persistent, on-chip sinc weights)",
+                          "bound": "tensor", "achieved": achieved, "peak": peak,
+                          "unit": "TFLOP/s", "frac": achieved / peak,
+                          "algorithmic": f"sum 2*J*S*L = {flops:.4g} flop per launch",
+                          "peak_source": f"measured bf16 {bf16_peak:.1f} TFLOP/s ({peak_src})"
+                                         + (" / 3 products" if prec == "fp32" else "")}),
         }
         batch.close()
         for p in plans:

@@ -160,6 +160,7 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
             }
         }
         lay.tile_steps = (int)streamed;
+        lay.total_steps = (int)total;
     }
 
     // Fixed-point TDOA: the largest xf <= 24 with (max|x| + 2) 2^xf < 2^31.
@@ -434,7 +435,7 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
                                   lay.J_pad, lay.J, lay.Q, h->d_nq, lay.n_aux, lay.xf, lay.Sc,
                                   lay.L_pad, L, h->precision, h->mode == SRP_MODE_CONV ? 1 : 0,
                                   lay.K, d_maps, h->d_part, lay.n_tiles, h->d_status, h->d_w,
-                                  h->d_woff, lay.tile_steps, s),
+                                  h->d_woff, lay.tile_steps, lay.tile_steps == lay.total_steps, s),
                  "tensor-core map kernel");
     } else if (h->mode == SRP_MODE_NYQUIST) {
         SRP_CUDA(launch_interp_simt(h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq, h->d_off, lay.n_aux,

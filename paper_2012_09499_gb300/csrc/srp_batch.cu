@@ -65,6 +65,7 @@ struct BatchInst {
     const uint4 *w;           // resident interpolation matrix of the plan, or null
     const int32_t *woff;      // [n_chunks] first 16-slot step of each chunk in a tile
     int tile_steps;           // 16-slot steps per tile of w
+    int all_streamed;         // every chunk's weights are resident: no TDOA table reads
     int pblocks;              // pair blocks of kPairBlock per frame
     int64_t op_row0;          // first block of the plan in the operand kernel's grid
     int64_t frame0;           // first block of the plan in the argmax kernel's grid
@@ -337,7 +338,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
         int64_t ljp = 0;
         auto load_next = [&]() {
             if (lq == 0) {
-                while (li < it1 && !live(a.items[li])) li += a.items[li].w;
+                // dead items, and items of plans whose weights are all resident,
+                // read no TDOA table
+                // (both hold for a whole (plan, frame tile) run)
+                while (li < it1 && (!live(a.items[li]) ||
+                                    (!kConv && !kTm && a.inst[a.items[li].x].all_streamed)))
+                    li += a.items[li].w;
                 if (li < it1) {
                     const int4 it = a.items[li];
                     const BatchInst &I = a.inst[it.x];
@@ -454,6 +460,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
             const int n_chunks = I.n_chunks, xf = I.xf;
             const int4 *ctab = I.ctab;
             const bool resident = !kConv && !kTm && I.w != nullptr;  // some chunks streamed
+            const bool skip_ring = resident && I.all_streamed;      // no weights generated
             int q = -1;
             float sp = 0.0f, f = 0.5f, x0f = 0.0f;
             int x0m = 0;
@@ -465,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                 const int st = g % a.stages;
                 const uint32_t ph = (uint32_t)(g / a.stages) & 1u;
                 const int4 nxt = __ldg(&ctab[c + 1 < n_chunks ? c + 1 : c]);
-                if (cur.x != q) {  // uniform: a new pair starts with this chunk
+                if (cur.x != q && !skip_ring) {  // uniform: a new pair starts with this chunk
                     q = cur.x;
                     int x0;
                     decode_tdoa(nX, xf, x0, f);
@@ -1050,6 +1057,7 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         I.w = static_cast<const uint4 *>(p->d_w);
         I.woff = p->d_woff;
         I.tile_steps = L.tile_steps;
+        I.all_streamed = (p->d_w != nullptr && L.tile_steps == L.total_steps) ? 1 : 0;
         if (p->d_w != nullptr) b->any_resident = true;
         I.max_frames = L.L_max;
         I.pblocks = (L.Q + kPairBlock - 1) / kPairBlock;

@@ -30,6 +30,7 @@ struct Layout {
     // tensor-core lag layout: pair q owns ceil(N'_q / 64) chunks of 64 slots
     int Sc = 0, n_chunks = 0, N_tc = 0, par1_used = 0;
     int tile_steps = 0;  // resident interpolation matrix: 16-slot steps per tile (0: generated)
+    int total_steps = 0; // 16-slot steps holding lags, per tile, of all pairs (resident plans)
     std::vector<char> streamed;  // per pair: its weights are resident and streamed
     bool tc = false;    // the Nyquist map runs on the tensor cores
     std::vector<int32_t> offc;
@@ -141,7 +142,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
                              int conv, int K, float *maps, unsigned long long *part, int n_tiles,
                              int *status, const void *w, const int32_t *woff, int tile_steps,
-                             cudaStream_t s);
+                             int all_streamed, cudaStream_t s);
 // Plan time: the resident interpolation matrix (operand A) of every tile.
 cudaError_t launch_build_w(const int2 *xs, const int4 *ctab, const int32_t *woff, int n_chunks,
                            int64_t J_pad, int xf, int tile_steps, int n_tiles, int precision,

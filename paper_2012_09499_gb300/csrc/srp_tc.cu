@@ -138,6 +138,7 @@ struct TcArgs {
     const uint4 *w;         // resident operand A (kW): the plan's interpolation matrix
     const int32_t *woff;    // [n_chunks] first 16-slot step of chunk c within a tile's block
     int tile_steps;         // 16-slot steps per 128-candidate tile
+    int all_streamed;       // kW with every chunk resident: the generators read no TDOA table
 };
 
 // ---------------------------------------------------------------------------
@@ -251,7 +252,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
         {
         // ---------------- A generation: one candidate row per thread ----------------
         // (kW: chunks whose weights are resident are streamed by the TMA warp and
-        // only pass through the stage barriers here)
+        // only pass through the stage barriers here; with every chunk resident the
+        // TDOA table is not read at all)
         const int64_t i = (int64_t)blockIdx.x * 128 + r;
         const uint32_t row = (uint32_t)r * 128u, sw = (uint32_t)(r & 7);
         // d = f + (m - e) for lag e of a group, where m = x0 + nmax - (first lag
@@ -266,9 +268,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
         // sits in slot p % kXRing.  Pair q + 1 is read from its slot when pair q
         // starts, one chunk or more ahead of its use, and that read issues the
         // load of pair q + 1 + kXAhead (one commit group per pair).
+        const int ring_q = (kW && a.all_streamed) ? 0 : a.Q;  // pairs whose TDOAs are read
 #pragma unroll
         for (int k = 0; k < kXAhead; ++k) {
-            if (k < a.Q)
+            if (k < ring_q)
                 cp_async8(xring + (uint32_t)(k * 128 + r) * 8u, &a.xs[(size_t)k * a.J_pad + i]);
             cp_async_commit();
         }
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                          : "=r"(nX), "=r"(nsp)
                          : "r"(xring + (uint32_t)((p % kXRing) * 128 + r) * 8u));
             const int pn = p + kXAhead;
-            if (pn < a.Q)
+            if (pn < ring_q)
                 cp_async8(xring + (uint32_t)((pn % kXRing) * 128 + r) * 8u,
                           &a.xs[(size_t)pn * a.J_pad + i]);
             cp_async_commit();
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             const int st = c % a.stages;
             const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
             const int4 nxt = __ldg(&a.ctab[c + 1 < a.n_chunks ? c + 1 : c]);
-            if (cur.x != q) {  // uniform: a new pair starts with this chunk
+            if (cur.x != q && ring_q > 0) {  // uniform: a new pair starts with this chunk
                 q = cur.x;
                 int x0;
                 decode_tdoa(nX, a.xf, x0, f);
@@ -608,7 +611,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
                              int conv, int K, float *maps, unsigned long long *part, int n_tiles,
                              int *status, const void *w, const int32_t *woff, int tile_steps,
-                             cudaStream_t s) {
+                             int all_streamed, cudaStream_t s) {
     // N is the plan's frames per CTA: the height of the tensor map's box.
     if (L == 0) return cudaSuccess;
     if (w != nullptr && conv) return cudaErrorInvalidValue;  // resident A: Nyquist only
@@ -676,6 +679,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.w = static_cast<const uint4 *>(w);
     a.woff = woff;
     a.tile_steps = tile_steps;
+    a.all_streamed = (w != nullptr && all_streamed) ? 1 : 0;
     const int grid_y = (L + N - 1) / N;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(xi_map);
     if (conv) {
