@@ -295,6 +295,13 @@ typedef struct {
     int32_t operand_a;       /* where the generated operand A lives: 1 = tensor memory
                                 (the MMAs read only B from shared memory), 2 = shared
                                 memory; 0 = tensor memory where it fits */
+    int32_t accumulators;    /* accumulators per work item: 2 = two MMA-issuing warps,
+                                each summing every other 16-slot step into its own
+                                accumulator (the epilogue adds the two); 1 = one warp and
+                                one accumulator (half the TMEM columns), refused for an
+                                FP32 batch whose longest reduction would accumulate a
+                                TMEM rounding bias above 5e-5 in one accumulator; 0 = 2
+                                where the tile fits, else 1 */
 } srp_batch_tiles;
 
 typedef struct {

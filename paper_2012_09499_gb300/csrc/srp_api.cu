@@ -24,7 +24,6 @@ constexpr int kMaxK = 8192;
 constexpr int kMaxFrames = 65536;
 constexpr int64_t kMaxJ = (int64_t)INT32_MAX - (1 << 20);
 constexpr int kMaxLagSpan = 8192;  // 2 (N_q + N_aux) + 1 per pair
-constexpr double kTcAccumBias = 1.5e-8;  // relative, per MMA step accumulated in TMEM
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
@@ -115,14 +114,16 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     // CUDA-core engine is FP32 only.  FP32 accumulation in TMEM carries a
     // systematic relative bias of about kTcAccumBias per accumulated MMA step
     // (measured on GB300), so an FP32 plan whose reduction is long enough for
-    // that bias to reach half of the 1e-4 tolerance (long conventional sums:
-    // many pairs x many bins) runs on the exact CUDA-core kernels instead.
+    // that bias to reach kTcBiasLimit, half of the 1e-4 tolerance (long
+    // conventional sums: many pairs x many bins), runs on the exact CUDA-core
+    // kernels instead.
     lay.tc = d->engine == SRP_ENGINE_AUTO;
-    if (lay.tc && d->precision == SRP_PREC_FP32) {
+    if (lay.tc) {
         int64_t steps = 0;  // 16-slot MMA steps per tile
         for (int q = 0; q < lay.Q; ++q) steps += round_up(tc_span(d, lay, q), 16) / 16;
+        lay.mma_steps = (int)std::min<int64_t>(steps, INT32_MAX);
         const double adds = 3.0 * (double)steps / 2.0;  // 3 products, 2 accumulators
-        if (adds * kTcAccumBias > 5e-5) lay.tc = false;
+        if (d->precision == SRP_PREC_FP32 && adds * kTcAccumBias > kTcBiasLimit) lay.tc = false;
     }
     if (!lay.tc && d->precision != SRP_PREC_FP32)
         return fail(SRP_ERR_UNSUPPORTED, "BF16/FP16 need the tensor-core engine");

@@ -90,6 +90,7 @@ struct PersistArgs {
     int N, stages;
     uint32_t idesc, tmem_cols;
     uint32_t a_col0;        // operand A in TMEM: first column of the A stages
+    int mma_warps;          // MMA-issuing warps, each with its own accumulator (1 or 2)
     int *status;
 };
 
@@ -264,8 +265,9 @@ __device__ __forceinline__ void sync_128() { asm volatile("bar.sync 1, 128;" :::
 // The persistent contraction.  Warps 0-3 generate operand A (one candidate
 // row per thread) and run the epilogue of the previous item after the
 // operands of the current one; warp 4 issues the TMA loads of B; warps 5-6
-// issue the MMAs by 16-slot step parity into two accumulators.  TMEM holds
-// two such accumulator pairs (item parity), columns [b 2N, b 2N + 2N).
+// issue the MMAs by 16-slot step parity into two accumulators (or warp 5
+// alone into one, mma_warps = 1).  TMEM holds two such accumulator sets (item
+// parity), columns [b W N, b W N + W N) for W = mma_warps.
 // ---------------------------------------------------------------------------
 // kTm: operand A is generated into TMEM after the accumulators (32 columns per
 // stage and part) and the MMAs read only B from shared memory.
@@ -311,13 +313,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(full_bar(s), 128 + 1);
-            mbar_init(empty_bar(s), 2);
+            mbar_init(empty_bar(s), a.mma_warps);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(acc_full(b), 2);
+            mbar_init(acc_full(b), a.mma_warps);
             mbar_init(acc_empty(b), 128);
         }
-        mbar_init(drain, 2);
+        mbar_init(drain, a.mma_warps);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -384,8 +386,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
             tc_fence_after();
             const BatchInst &I = a.inst[P.x];
             const BatchCall &C = a.call[P.x];
-            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 2 * N);
-            const int par1 = I.par1_used;
+            const uint32_t trow =
+                tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * a.mma_warps * N);
+            const int par1 = a.mma_warps == 2 && I.par1_used;
             for (int j0 = 0; j0 < N; j0 += 16) {
                 float v[16];
                 tmem_ld16(trow + (uint32_t)j0, v);
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                 for (int jj = 0; jj < 16; ++jj) mt[(j0 + jj) * kMtStride + r] = v[jj];
             }
             tc_fence_before();
-            mbar_arrive(acc_empty(b));  // accumulator pair b may be overwritten
+            mbar_arrive(acc_empty(b));  // accumulator set b may be overwritten
             sync_128();
             const int64_t J = I.J, tile0 = (int64_t)P.y * 128;
             const int l0 = P.z, n_rows = min(N, C.L - l0);
@@ -588,8 +591,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
         }
     } else {
         // ---------------- MMA issue ----------------
-        const int par = warp - kMmaWarp0;
-        if (lane == 0) {
+        const int par = warp - kMmaWarp0, nw = a.mma_warps;
+        if (lane == 0 && par < nw) {
             int g = 0, kx = 0;
             bool ok = true;
             for (int t = it0; t < it1 && ok; ++t) {
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                 if (!mbar_wait(acc_empty(b), ((uint32_t)(kx >> 1) & 1u) ^ 1u, abort_flag, a.status))
                     break;
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(b * 2 * N + par * N);
+                const uint32_t dt = tmem + (uint32_t)((b * nw + par) * N);
                 uint32_t acc = 0;  // the item's first MMA overwrites the accumulator
                 const int n_chunks = I.n_chunks;
                 const int4 *ctab = I.ctab;
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                     const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
                     const int nk = __ldg(&ctab[c]).w;
                     const bool streamed = resident && __ldg(&I.woff[c]) >= 0;
-                    for (int kk = par; kk < nk; kk += 2) {
+                    for (int kk = par; kk < nk; kk += nw) {
                         const uint64_t adv = (uint64_t)(kk * 2);
                         const uint32_t ac = (uint32_t)(kk * 8);
                         if (kTm) {
@@ -678,6 +681,7 @@ namespace {
 struct TileChoice {
     int N = 0, stages = 0, cps = 0;
     bool tm = false;  // operand A in TMEM
+    int mw = 2;       // MMA-issuing warps = accumulators per item
 };
 
 // Bytes of shared memory of the persistent kernel for a tile choice.
@@ -686,19 +690,22 @@ size_t persist_smem(const TileChoice &t, bool split) {
     return 2048 + stage * t.stages + (size_t)kXRing * 128 * 8 + (size_t)t.N * kMtStride * 4;
 }
 
-// TMEM columns: two accumulator pairs (4N) and, with A in TMEM, 32 per stage
-// and part; rounded up to a power of two (the allocation unit).
+// TMEM columns: two accumulator sets of mw accumulators (2 mw N) and, with A
+// in TMEM, 32 per stage and part; rounded up to a power of two (the
+// allocation unit).
 uint32_t persist_tmem_cols(const TileChoice &t, bool split) {
-    const uint32_t need = (uint32_t)(4 * t.N) + (t.tm ? (uint32_t)(t.stages * (split ? 2 : 1) * 32) : 0u);
+    const uint32_t need = (uint32_t)(2 * t.mw * t.N) +
+                          (t.tm ? (uint32_t)(t.stages * (split ? 2 : 1) * 32) : 0u);
     uint32_t cols = 32;
     while (cols < need) cols <<= 1;
     return cols;
 }
 
-bool tile_fits(const TileChoice &t, bool split, bool any_resident) {
+bool tile_fits(const TileChoice &t, bool split, bool any_resident, bool one_acc) {
     if (t.N < 16 || t.N > 256 || (t.N & 15)) return false;
     if (t.tm && any_resident) return false;  // streamed A blocks live in shared memory
     if (t.stages < 2 || t.stages > kMaxStages || t.cps < 1 || t.cps > 2) return false;
+    if (t.mw < 1 || t.mw > 2 || (t.mw == 1 && !one_acc)) return false;
     if (persist_tmem_cols(t, split) * (uint32_t)t.cps > 512u) return false;
     const size_t smem = persist_smem(t, split);
     if (smem > (size_t)kMaxSmemCta) return false;
@@ -721,6 +728,7 @@ struct srp_batch_s {
     bool split = false, half = false;
     int max_L = 0, max_K = 0;
     bool any_resident = false;  // some plan streams its interpolation matrix: A in shared memory
+    bool one_acc = true;        // one accumulator per item keeps the FP32 bias within its limit
     TileChoice tiles;
     int n_ctas = 0, n_items = 0;
     int64_t op_blocks = 0, frame_blocks = 0, b_rows = 0;
@@ -903,7 +911,8 @@ srp_status batch_configure(srp_batch_s *b, const TileChoice &t) {
     const uint32_t ab = b->half ? 0u : 1u;
     pa.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(t.N >> 3) << 17) | ((128u >> 4) << 24);
     pa.tmem_cols = persist_tmem_cols(t, b->split);
-    pa.a_col0 = (uint32_t)(4 * t.N);
+    pa.a_col0 = (uint32_t)(2 * t.mw * t.N);
+    pa.mma_warps = t.mw;
     pa.status = b->d_status;
     // shared memory at launch: at least enough that no more than cps CTAs fit
     // on one SM (so that their TMEM columns always fit, 512 per SM)
@@ -1059,6 +1068,9 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         I.tile_steps = L.tile_steps;
         I.all_streamed = (p->d_w != nullptr && L.tile_steps == L.total_steps) ? 1 : 0;
         if (p->d_w != nullptr) b->any_resident = true;
+        // FP32 split: 3 products per step, all in one accumulator
+        if (p0->precision == SRP_PREC_FP32 && 3.0 * L.mma_steps * kTcAccumBias > kTcBiasLimit)
+            b->one_acc = false;
         I.max_frames = L.L_max;
         I.pblocks = (L.Q + kPairBlock - 1) / kPairBlock;
         part += sizeof(unsigned long long) * (size_t)L.L_max * L.n_tiles;
@@ -1103,18 +1115,26 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
     const bool given_cps = tiles != nullptr && tiles->ctas_per_sm != 0;
     const int given_a = tiles != nullptr ? tiles->operand_a : 0;
     if (given_a < 0 || given_a > 2) return bail(fail(SRP_ERR_INVALID_ARG, "operand_a must be 0, 1 or 2"));
+    const int given_mw = tiles != nullptr ? tiles->accumulators : 0;
+    if (given_mw < 0 || given_mw > 2)
+        return bail(fail(SRP_ERR_INVALID_ARG, "accumulators must be 0, 1 or 2"));
     TileChoice best;
     for (int tm = 1; tm >= 0; --tm) {  // A in TMEM first
         if ((given_a == 1 && !tm) || (given_a == 2 && tm)) continue;
         for (int cps = 2; cps >= 1; --cps) {
             if (given_cps && cps != tiles->ctas_per_sm) continue;
-            for (int st = 4; st >= 2; --st) {
-                if (given_stages && st != tiles->stages) continue;
-                TileChoice c = t;
-                c.cps = cps;
-                c.stages = st;
-                c.tm = tm != 0;
-                if (tile_fits(c, b->split, b->any_resident) && best.N == 0) best = c;
+            for (int mw = 2; mw >= 1; --mw) {
+                if (given_mw != 0 && mw != given_mw) continue;
+                for (int st = 4; st >= 2; --st) {
+                    if (given_stages && st != tiles->stages) continue;
+                    TileChoice c = t;
+                    c.cps = cps;
+                    c.stages = st;
+                    c.tm = tm != 0;
+                    c.mw = mw;
+                    if (tile_fits(c, b->split, b->any_resident, b->one_acc) && best.N == 0)
+                        best = c;
+                }
             }
         }
     }
@@ -1147,7 +1167,8 @@ srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const int32_t *L
     srp_status st = batch_call_table(b, d_in, L, d_maps, d_argmax, d_peak);
     if (st != SRP_OK) return st;
     // candidates: frames per item N in {16, 32, 64, 128, 256} up to the
-    // largest call, pipeline depth 2..4, one or two CTAs per SM
+    // largest call, pipeline depth 2..4, one or two CTAs per SM, A in TMEM or
+    // shared memory, one or two accumulators
     int maxl = 0;
     for (size_t i = 0; i < b->plans.size(); ++i) maxl = std::max(maxl, L[i]);
     const int nmax = std::min(256, round_up_int(std::max(maxl, 1), 16));
@@ -1165,13 +1186,15 @@ srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const int32_t *L
         if (result != SRP_OK) break;
         for (int tm = 0; tm <= 1 && result == SRP_OK; ++tm)
         for (int cps = 1; cps <= 2 && result == SRP_OK; ++cps)
+        for (int mw = 1; mw <= 2 && result == SRP_OK; ++mw)
             for (int stg = 2; stg <= 4 && result == SRP_OK; ++stg) {
                 TileChoice c;
                 c.N = N;
                 c.stages = stg;
                 c.cps = cps;
                 c.tm = tm != 0;
-                if (!tile_fits(c, b->split, b->any_resident)) continue;
+                c.mw = mw;
+                if (!tile_fits(c, b->split, b->any_resident, b->one_acc)) continue;
                 if ((result = batch_configure(b, c)) != SRP_OK) break;
                 float ms = 0.0f;
                 for (int rep = 0; rep < 3 && result == SRP_OK; ++rep) {
@@ -1212,6 +1235,7 @@ srp_status srp_batch_get_info(srp_batch b, srp_batch_info *info) {
     info->tiles.stages = b->tiles.stages;
     info->tiles.ctas_per_sm = b->tiles.cps;
     info->tiles.operand_a = b->tiles.tm ? 1 : 2;
+    info->tiles.accumulators = b->tiles.mw;
     info->launches = 3;
     info->tuned = b->tuned;
     info->tuned_ms = b->tuned_ms;

@@ -22,6 +22,13 @@ constexpr int kLagPad = 64;
 enum Stage { kStagePhat = 0, kStageGcc = 1, kStageMap = 2, kStageArgmax = 3, kNumStages = 4 };
 
 // Host-side sizes of a plan; shared by describe / footprint / plan.
+// FP32 accumulation in TMEM carries a systematic relative bias of about
+// kTcAccumBias per MMA accumulated into one accumulator (measured on GB300);
+// FP32 tensor-core paths keep that bias below kTcBiasLimit, half of the 1e-4
+// tolerance of the FP32 maps.
+constexpr double kTcAccumBias = 1.5e-8;
+constexpr double kTcBiasLimit = 5e-5;
+
 struct Layout {
     int M = 0, Q = 0, K = 0, Kb = 0, n_aux = 0, S = 0, S_pad = 0, max_nq = 0, xf = 0;
     int64_t J = 0, J_pad = 0;
@@ -29,6 +36,7 @@ struct Layout {
     std::vector<int32_t> Nq, off, pm, pmp;  // per pair
     // tensor-core lag layout: pair q owns ceil(N'_q / 64) chunks of 64 slots
     int Sc = 0, n_chunks = 0, N_tc = 0, par1_used = 0;
+    int mma_steps = 0;   // tensor-core plans: 16-slot MMA steps per tile over all pairs
     int tile_steps = 0;  // resident interpolation matrix: 16-slot steps per tile (0: generated)
     int total_steps = 0; // 16-slot steps holding lags, per tile, of all pairs (resident plans)
     std::vector<char> streamed;  // per pair: its weights are resident and streamed

@@ -56,7 +56,8 @@ class srp_plan_info(ctypes.Structure):
 
 class srp_batch_tiles(ctypes.Structure):
     _fields_ = [("frames_per_tile", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("operand_a", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("operand_a", ctypes.c_int32),
+                ("accumulators", ctypes.c_int32)]
 
 
 class srp_batch_info(ctypes.Structure):
@@ -353,12 +354,13 @@ def _ptr_array(items):
 
 def srp_batch_create(handles, tiles=None):
     """Batch over plan handles; tiles = (frames_per_tile, stages, ctas_per_sm
-    [, operand_a: 1 TMEM, 2 shared memory]), zeros for defaults, or None."""
+    [, operand_a: 1 TMEM, 2 shared memory [, accumulators: 1 or 2]]), zeros for
+    defaults, or None."""
     hs = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
                                             for h in handles])
     t = None
     if tiles is not None:
-        t = srp_batch_tiles(*[int(v) for v in tiles] + [0] * (4 - len(tiles)))
+        t = srp_batch_tiles(*[int(v) for v in tiles] + [0] * (5 - len(tiles)))
     b = ctypes.c_void_p()
     _check(lib().srp_batch_create(hs, len(handles), ctypes.byref(t) if t is not None else None,
                                   ctypes.byref(b)), "srp_batch_create")

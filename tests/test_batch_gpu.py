@@ -155,6 +155,41 @@ def test_batch_tuner_and_explicit_tiles():
         assert np.array_equal(m1, m2) and np.array_equal(a1, a2)
 
 
+def test_one_and_two_accumulators_agree():
+    """The 16-slot steps summed by one MMA warp into one accumulator, or by two
+    warps into two that the epilogue adds, give the same maps up to the order
+    of the FP32 sums; with 64 frames per item and A in tensor memory only the
+    single accumulator lets two CTAs share an SM, and the default picks it."""
+    cfgs = small_mix(6, 3, (3000, 9000), 64)
+    L = [64, 40, 64]
+    for precision in ("fp32", "bf16"):
+        plans = make_plans(cfgs, "nyquist", precision, 64)
+        refs = [oracle_maps(c, "nyquist", l) for c, l in zip(cfgs, L)]
+        outs = {}
+        for mw in (1, 2):
+            b = srp.Batch(plans, tiles=(32, 2, 2, 1, mw))
+            assert (b.info.tiles.operand_a, b.info.tiles.accumulators) == (1, mw)
+            outs[mw] = run_batch(b, cfgs, L)
+            for (m, a, p), ref in zip(outs[mw], refs):
+                check(m, a, p, ref, TOL[precision], exact_argmax=precision == "fp32")
+            b.close()
+        # the FP32 accumulation bias of tcgen05 (about 1.5e-8 relative per MMA
+        # into one accumulator) grows with the steps one accumulator sums
+        steps = max(p.info.S // 16 + p.info.Q for p in plans)  # 16-lag steps, padded per pair
+        bound = 4 * 3 * steps * 1.5e-8 if precision == "fp32" else 1e-2
+        for (m1, _, _), (m2, _, _) in zip(outs[1], outs[2]):
+            pk = np.abs(m2).max(axis=1, keepdims=True)
+            assert np.all(np.abs(m1 - m2) <= bound * pk), (np.abs(m1 - m2) / pk).max()
+        b = srp.Batch(plans, tiles=(64, 0, 2, 1))
+        t = b.info.tiles
+        assert (t.ctas_per_sm, t.accumulators) == (2, 1)
+        for (m, a, p), ref in zip(run_batch(b, cfgs, L), refs):
+            check(m, a, p, ref, TOL[precision], exact_argmax=precision == "fp32")
+        b.close()
+        for pl in plans:
+            pl.close()
+
+
 def test_batch_full_scale_sampled():
     """Arrays of the uneven mix at full size (J up to 500k, K up to 2048,
     M up to 16): sampled candidates and frames against the oracle."""
