@@ -354,6 +354,7 @@ def bench_ours(args):
         extra["serving"] = bench_serving(args)
     if world == 1 and not args.no_paper:
         extra["paper_setup"] = bench_paper_setup(args, flush, stream)
+        extra["complexity"] = bench_complexity(args, flush, stream)
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline(mic, grid, Ys[0], w, Q, S)
@@ -581,6 +582,68 @@ def bench_paper_setup(args, flush, stream):
                                                   "frac_zero": float(np.mean(gap < 1e-3))},
             "ms_per_32_frames": ms, "value": 8101 * 15 * PAPER_L / (ms * 1e-3), "unit": UNIT}
     return out
+
+
+COMPLEXITY_RADII = (0.025, 0.05, 0.1, 0.2, 0.3, 0.5)
+COMPLEXITY_L = 64
+
+
+def bench_complexity(args, flush, stream):
+    """The complexity reduction factors of Sec. 3.3 against the array radius
+    (the setting of Fig. 2: M = 6 on a circle, c = 340 m/s, fs = 16 kHz), from
+    srp_plan_complexity, beside the measured GPU time ratios on the far-field
+    half sphere at 2 degrees (J = 8101, K = 2048, K_b = 1024, N_aux = 2, FP32,
+    64 frames): t_samp = the GCC-sample stage, t_int = the Nyquist map stage,
+    t_conv = the conventional map stage (tensor cores).  Fig. 2's own J values
+    are not in the paper's source, so R_samp is also given for J = 1e3, 1e4
+    and 1e5 from the same N."""
+    import torch
+
+    from paper_2012_09499_gb300 import srp, synth
+    grid = synth.half_sphere_directions(2.0)
+    rng = np.random.default_rng(5)
+    Kb = 1025
+    Y = torch.from_numpy((rng.standard_normal((COMPLEXITY_L, 6, Kb)) +
+                          1j * rng.standard_normal((COMPLEXITY_L, 6, Kb))).astype(np.complex64)).cuda()
+    rows = []
+    for r in COMPLEXITY_RADII:
+        mic = synth.circular_array(6, r)
+        row = {"radius_m": r}
+        for naux in (0, 1, 2):
+            d, keep = srp.make_desc(mic, grid, 16000.0, 340.0, 2048, mode="nyquist", n_aux=naux,
+                                    far_field=True)
+            cx = srp.srp_plan_complexity(d)
+            row[f"N_aux_{naux}"] = {"N": cx["N"], "R_samp_J8101": cx["R_samp"],
+                                    "R_samp_by_J": {str(J): cx["N"] / J for J in (1000, 10000, 100000)}}
+            if naux == 2:
+                row.update({"R_samp": cx["R_samp"], "R_int": cx["R_int"], "R": cx["R"],
+                            "C_samp": cx["C_samp"], "C_int": cx["C_int"], "C_conv": cx["C_conv"]})
+        t = {}
+        for mode in ("nyquist", "conventional"):
+            plan = srp.Plan(mic, grid, 16000.0, 340.0, 2048, mode=mode, n_aux=2, far_field=True,
+                            max_frames=COMPLEXITY_L)
+            srp.srp_set_timing(plan.handle)
+            maps = torch.empty((COMPLEXITY_L, grid.shape[0]), dtype=torch.float32, device="cuda")
+            am = torch.empty(COMPLEXITY_L, dtype=torch.int32, device="cuda")
+
+            def step(k, plan=plan, maps=maps, am=am):
+                srp.srp_map(plan.handle, Y, COMPLEXITY_L, maps, am, None, stream)
+            _, st, _ = time_steps(step, 10, args.warmup, flush, stream, 1,
+                                  timed_stage=lambda plan=plan: srp.srp_stage_times(plan.handle),
+                                  name=f"complexity_{mode}_{r}")
+            srp.srp_poll_device_status(plan.handle)
+            t[mode] = {k: float(np.mean([x[k] for x in st])) for k in st[0]}
+            if mode == "conventional":
+                t["conv_engine"] = "tensor cores" if plan.info.tensor_cores else "cuda cores"
+            plan.close()
+        ts, ti, tc = t["nyquist"]["gcc_samples"], t["nyquist"]["map"], t["conventional"]["map"]
+        row["measured_ms"] = {"t_samp": ts, "t_int": ti, "t_conv": tc, "conv_engine": t["conv_engine"]}
+        row["measured_ratio"] = {"samp": ts / tc, "int": ti / tc, "total": (ts + ti) / tc}
+        rows.append(row)
+    return {"workload": ("M = 6 circle of the given radius, c = 340 m/s, fs = 16 kHz, far-field half "
+                         "sphere at 2 deg (J = 8101), K = 2048 (K_b = 1024), N_aux = 2 for R and the "
+                         f"timings, FP32, {COMPLEXITY_L} frames, L2 flushed between steps"),
+            "radii": rows}
 
 
 def serve_run(srp, plans, cfgs, rate, duration, seed):

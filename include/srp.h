@@ -155,6 +155,29 @@ typedef struct srp_plan_s *srp_handle;
  * Eq. SRPapprox with T = 1/fs.  Host only: touches no device.            */
 SRP_API srp_status srp_plan_describe(const srp_plan_desc *d, srp_plan_info *info, int32_t *Nq_out);
 
+/* Operation counts of Sec. 3.3 (and of Sec. 2.3 for the conventional map)
+ * for a descriptor, as the paper defines them, with P = Q pairs and K_b =
+ * K / 2 one-sided bins (a 2048-point DFT gives K_b = 1024, the paper's K):
+ *   N      = (2/P) sum_q N_q + 2 N_aux + 1   critical samples per pair
+ *   C_samp = N P K_b   complex multiplications of the partial IDFT
+ *   C_int  = N P J     real multiplications of the sinc interpolation
+ *   C_conv = J P K_b   complex multiplications of the conventional map
+ *   R_samp = N / J,  R_int = N / K_b,  R = R_samp + R_int.
+ * N_aux of the descriptor is used in either mode.  The counts are per frame
+ * and are not the operation counts of this library's kernels.  Host only:
+ * touches no device.  Errors: those of srp_plan_describe; NULL out is
+ * SRP_ERR_INVALID_ARG.                                                     */
+typedef struct {
+    double N;            /* average critical samples per pair */
+    int32_t P;           /* microphone pairs */
+    int32_t K_b;         /* one-sided frequency bins, K / 2 */
+    int64_t J;           /* candidates */
+    double C_samp, C_int, C_conv;
+    double R_samp, R_int, R;
+} srp_complexity;
+
+SRP_API srp_status srp_plan_complexity(const srp_plan_desc *d, srp_complexity *out);
+
 /* Device bytes srp_plan would allocate for d (host only).                */
 SRP_API srp_status srp_plan_footprint(const srp_plan_desc *d, size_t *device_bytes);
 

@@ -102,6 +102,22 @@ def lag_counts(mic_xyz, fs: float, c: float):
     return Nq, d
 
 
+def complexity(mic_xyz, fs: float, c: float, K_b: int, J: int, n_aux: int):
+    """Operation counts of Sec. 3.3 (C_conv of Sec. 2.3) for one frame, with
+    K_b one-sided frequency bins (the paper's K): the average number of
+    critical samples per pair N = (2/P) sum N_q + 2 N_aux + 1, C_samp = N P K_b
+    complex multiplications of the partial IDFT, C_int = N P J real
+    multiplications of the interpolation, C_conv = J P K_b, and the reduction
+    factors R_samp = C_samp / C_conv, R_int = C_int / C_conv, R = their sum."""
+    Nq, _ = lag_counts(mic_xyz, fs, c)
+    P = len(Nq)
+    N = 2.0 / P * float(np.sum(Nq, dtype=np.int64)) + 2.0 * n_aux + 1.0
+    C_samp, C_int, C_conv = N * P * K_b, N * P * J, float(J) * P * K_b
+    return {"N": N, "P": P, "K_b": K_b, "J": J, "C_samp": C_samp, "C_int": C_int,
+            "C_conv": C_conv, "R_samp": C_samp / C_conv, "R_int": C_int / C_conv,
+            "R": (C_samp + C_int) / C_conv}
+
+
 def tdoa(mic_xyz, grid_xyz, fs: float, c: float, far_field: bool = False):
     """TDOAs in samples, [J][Q] (Eq. Deltat_i or Eq. Deltat_i_spher)."""
     mic = _c64(mic_xyz)

@@ -486,6 +486,30 @@ srp_status srp_plan_describe(const srp_plan_desc *d, srp_plan_info *info, int32_
     return SRP_OK;
 }
 
+srp_status srp_plan_complexity(const srp_plan_desc *d, srp_complexity *out) {
+    if (out == nullptr) return fail(SRP_ERR_INVALID_ARG, "out is NULL");
+    if (d == nullptr) return fail(SRP_ERR_INVALID_ARG, "descriptor is NULL");
+    Layout lay;
+    srp_status st = make_layout(d, lay);
+    if (st != SRP_OK) return st;
+    // Sec. 3.3: N averages the 2 N_q + 2 N_aux + 1 samples of each pair
+    int64_t sum_nq = 0;
+    for (int32_t v : lay.Nq) sum_nq += v;
+    const double P = (double)lay.Q, Kb = (double)(d->K / 2), J = (double)d->J;
+    memset(out, 0, sizeof *out);
+    out->N = 2.0 * (double)sum_nq / P + 2.0 * (double)d->n_aux + 1.0;
+    out->P = lay.Q;
+    out->K_b = d->K / 2;
+    out->J = d->J;
+    out->C_samp = out->N * P * Kb;
+    out->C_int = out->N * P * J;
+    out->C_conv = J * P * Kb;
+    out->R_samp = out->N / J;
+    out->R_int = out->N / Kb;
+    out->R = out->R_samp + out->R_int;
+    return SRP_OK;
+}
+
 srp_status srp_plan_footprint(const srp_plan_desc *d, size_t *device_bytes) {
     if (device_bytes == nullptr) return fail(SRP_ERR_INVALID_ARG, "device_bytes is NULL");
     Layout lay;

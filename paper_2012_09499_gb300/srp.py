@@ -54,6 +54,15 @@ class srp_plan_info(ctypes.Structure):
     ]
 
 
+class srp_complexity(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_double), ("P", ctypes.c_int32), ("K_b", ctypes.c_int32),
+        ("J", ctypes.c_int64), ("C_samp", ctypes.c_double), ("C_int", ctypes.c_double),
+        ("C_conv", ctypes.c_double), ("R_samp", ctypes.c_double), ("R_int", ctypes.c_double),
+        ("R", ctypes.c_double),
+    ]
+
+
 class srp_batch_tiles(ctypes.Structure):
     _fields_ = [("frames_per_tile", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("operand_a", ctypes.c_int32),
@@ -104,6 +113,7 @@ def lib():
         sigs = {
             "srp_plan_describe": [dp, ctypes.POINTER(srp_plan_info), vp],
             "srp_plan_footprint": [dp, ctypes.POINTER(ctypes.c_size_t)],
+            "srp_plan_complexity": [dp, ctypes.POINTER(srp_complexity)],
             "srp_plan": [dp, ctypes.POINTER(vp)],
             "srp_plan_get_info": [vp, ctypes.POINTER(srp_plan_info)],
             "srp_plan_tdoa": [vp, vp],
@@ -212,6 +222,13 @@ def srp_plan_describe(desc):
     _check(lib().srp_plan_describe(ctypes.byref(desc), ctypes.byref(info), nq.ctypes.data),
            "srp_plan_describe")
     return info, nq[: info.Q]
+
+
+def srp_plan_complexity(desc) -> dict:
+    """Operation counts and reduction factors of Sec. 3.3 for a descriptor."""
+    c = srp_complexity()
+    _check(lib().srp_plan_complexity(ctypes.byref(desc), ctypes.byref(c)), "srp_plan_complexity")
+    return {k: getattr(c, k) for k, _ in srp_complexity._fields_}
 
 
 def srp_plan_footprint(desc) -> int:

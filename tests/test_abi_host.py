@@ -79,6 +79,28 @@ def test_describe_paper_example():
         assert info.J == 8101
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_complexity_matches_oracle(seed):
+    """srp_plan_complexity (host only) gives the oracle's Sec. 3.3 counts, in
+    both modes, for random arrays and for the paper's circle."""
+    rng = np.random.default_rng(300 + seed)
+    M = int(rng.integers(2, 17))
+    cases = [(rng.uniform(-0.4, 0.4, (M, 3)), int(rng.integers(1, 5000)), 2 * int(rng.integers(8, 2049)),
+              int(rng.integers(0, 5)), mode) for mode in ("nyquist", "conventional")]
+    cases.append((synth.circular_array(6, 0.05 * (seed + 1)), 8101, 2048, seed % 3, "nyquist"))
+    for mic, J, K, naux, mode in cases:
+        grid = rng.uniform(-2, 2, (J, 3))
+        d, keep = srp.make_desc(mic, grid, 16000.0, 343.0, K, mode=mode, n_aux=naux)
+        got = srp.srp_plan_complexity(d)
+        ref = oracle.complexity(mic, 16000.0, 343.0, K // 2, J, naux)
+        assert (got["P"], got["K_b"], got["J"]) == (ref["P"], ref["K_b"], ref["J"])
+        for k in ("N", "C_samp", "C_int", "C_conv", "R_samp", "R_int", "R"):
+            assert got[k] == pytest.approx(ref[k], rel=1e-14, abs=0), k
+    with pytest.raises(srp.SrpError):
+        d, keep = _desc(K=7)
+        srp.srp_plan_complexity(d)
+
+
 def test_exact_integer_lag_bound():
     mic = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])
     d, keep = srp.make_desc(mic, np.zeros((1, 3)), 8192.0, 256.0, 64)

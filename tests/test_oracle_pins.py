@@ -54,19 +54,47 @@ def test_paper_complexity_example():
     K = 1024
     assert sorted(Nq.tolist()) == [4] * 6 + [8] * 6 + [9] * 3
 
-    def N_of(naux):
-        return 2.0 / P * Nq.sum() + 2 * naux + 1
-
+    c0, c1, c2 = (oracle.complexity(mic, 16000.0, 340.0, K, J, n) for n in (0, 1, 2))
     vals = {
-        "P": P, "J": J, "N_at_naux0": N_of(0), "N_slope_per_naux": N_of(1) - N_of(0),
-        "C_conv": J * P * K, "C_samp_naux2": N_of(2) * P * K, "C_int_naux2": N_of(2) * P * J,
-        "R_samp_naux2": N_of(2) / J, "R_int_naux2": N_of(2) / K,
+        "P": c2["P"], "J": J, "N_at_naux0": c0["N"], "N_slope_per_naux": c1["N"] - c0["N"],
+        "C_conv": c2["C_conv"], "C_samp_naux2": c2["C_samp"], "C_int_naux2": c2["C_int"],
+        "R_samp_naux2": c2["R_samp"], "R_int_naux2": c2["R_int"],
     }
+    assert c2["R"] == pytest.approx(c2["R_samp"] + c2["R_int"], rel=1e-15)
     for k, (v, tol) in gold.items():
         if tol == "exact":
             assert vals[k] == v, k
         else:
             assert abs(vals[k] - v) <= float(tol) + 1e-12 * abs(v), (k, vals[k], v)
+
+
+def test_complexity_circle_closed_form():
+    """Sec. 3.3 for an M = 6 circle of radius r (the setting of Fig. 2): the 15
+    chords are r (6 pairs), r sqrt(3) (6) and 2r (3), so N is a closed form in
+    r; R_samp grows with the radius, R_int = R_samp J / K_b, and R_samp falls
+    as 1/J at fixed r."""
+    fs, c, K_b = 16000.0, 340.0, 1024
+    prev = 0.0
+    for r in np.linspace(0.01, 0.5, 50):
+        mic = synth.circular_array(6, r)
+        f = lambda dist: np.floor(dist * fs / c)  # noqa: E731
+        for naux in (0, 1, 2):
+            N = 2.0 / 15.0 * (6 * f(r) + 6 * f(np.sqrt(3.0) * r) + 3 * f(2.0 * r)) + 2 * naux + 1
+            for J in (1000, 8101, 100000):
+                cx = oracle.complexity(mic, fs, c, K_b, J, naux)
+                # chord lengths computed from coordinates may round across an
+                # integer boundary: only then may N differ, by 2/15 per pair class
+                assert abs(cx["N"] - N) <= 2.0 / 15.0 * 6 + 1e-12
+                assert cx["R_samp"] == pytest.approx(cx["N"] / J, rel=1e-15)
+                assert cx["R_int"] == pytest.approx(cx["R_samp"] * J / K_b, rel=1e-12)
+        cx = oracle.complexity(mic, fs, c, K_b, 8101, 0)
+        assert cx["R_samp"] >= prev
+        prev = cx["R_samp"]
+    # away from integer boundaries the closed form is exact
+    for r in (0.03, 0.1, 0.23, 0.41):
+        cx = oracle.complexity(synth.circular_array(6, r), fs, c, K_b, 8101, 2)
+        f = lambda dist: np.floor(dist * fs / c)  # noqa: E731
+        assert cx["N"] == 2.0 / 15.0 * (6 * f(r) + 6 * f(np.sqrt(3.0) * r) + 3 * f(2 * r)) + 5
 
 
 def test_lag_count_exact_integer_boundary():
