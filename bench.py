@@ -355,6 +355,7 @@ def bench_ours(args):
     if world == 1 and not args.no_paper:
         extra["paper_setup"] = bench_paper_setup(args, flush, stream)
         extra["complexity"] = bench_complexity(args, flush, stream)
+        extra["refine"] = bench_refine(args, flush, stream)
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline(mic, grid, Ys[0], w, Q, S)
@@ -581,6 +582,72 @@ def bench_paper_setup(args, flush, stream):
             "maximiser_gap_to_conventional_deg": {"mean": float(gap.mean()),
                                                   "frac_zero": float(np.mean(gap < 1e-3))},
             "ms_per_32_frames": ms, "value": 8101 * 15 * PAPER_L / (ms * 1e-3), "unit": UNIT}
+    return out
+
+
+REFINE_LEVELS, REFINE_SHRINK, REFINE_STEP = 4, 0.5, 0.1
+
+
+def bench_refine(args, flush, stream):
+    """Coarse-to-fine search (the refinement Sec. 3.3 leaves outside the
+    paper's scope) against the full fine grid, on the same room_3d scene
+    (seed 0, 64 frames, one source): (a) the Nyquist FP32 map on the
+    100 x 80 x 60 grid at 0.05 m (J = 480000) and its argmax; (b) the map on
+    a 25 x 20 x 15 grid at 0.2 m (J = 7500), then srp_refine around each
+    frame's coarse maximiser with a 5 x 5 x 5 stencil of step 0.1 m over 4
+    levels halving the step (last step 0.0125 m).  Per path: ms per step (L2
+    flushed), points evaluated per frame and the median distance of the
+    found point to the source."""
+    import torch
+
+    from paper_2012_09499_gb300 import srp, synth
+    fine = synth.room_3d(seed=0)
+    coarse = synth.room_3d(seed=0, shape=(25, 20, 15), spacing=0.2)
+    assert np.array_equal(fine["Y"], coarse["Y"])
+    Y = torch.from_numpy(fine["Y"]).cuda()
+    L = fine["L"]
+    src = fine["sources"][0]
+    g = (np.arange(5) - 2.0) * REFINE_STEP
+    offs = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    out = {"workload": ("room_3d seed 0 (M = 8, one source at SNR 10 dB, K = 1024, L = 64), "
+                        "Nyquist FP32, N_aux = 2")}
+    plans = {}
+    for name, cfg in (("fine", fine), ("coarse", coarse)):
+        plans[name] = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"],
+                               mode="nyquist", n_aux=2, max_frames=L)
+    am = torch.empty(L, dtype=torch.int32, device="cuda")
+    pk = torch.empty(L, dtype=torch.float32, device="cuda")
+
+    def fine_step(k):
+        srp.srp_map(plans["fine"].handle, Y, L, None, am, pk, stream)
+    ms_f, _, _ = time_steps(fine_step, 10, args.warmup, flush, stream, 1, name="refine_fine")
+    err_f = np.linalg.norm(fine["grid"][am.cpu().numpy()] - src, axis=1)
+    ref = srp.Refiner(plans["coarse"], offs, levels=REFINE_LEVELS, shrink=REFINE_SHRINK)
+    xyz = torch.empty((L, 3), dtype=torch.float64, device="cuda")
+    val = torch.empty(L, dtype=torch.float32, device="cuda")
+
+    def coarse_step(k):
+        srp.srp_map(plans["coarse"].handle, Y, L, None, am, pk, stream)
+        srp.lib().srp_refine(ref.handle, L, am.data_ptr(), None, xyz.data_ptr(), val.data_ptr(),
+                             None, srp._stream(stream))
+    ms_c, _, _ = time_steps(coarse_step, 10, args.warmup, flush, stream, 1, name="refine_coarse")
+    srp.srp_poll_device_status(plans["coarse"].handle)
+    err_c = np.linalg.norm(xyz.cpu().numpy() - src, axis=1)
+    err_0 = np.linalg.norm(coarse["grid"][am.cpu().numpy()] - src, axis=1)
+    ref.close()
+    for p in plans.values():
+        p.close()
+    out["fine_grid"] = {"ms_per_step": float(ms_f.mean()), "points_per_frame": 480000,
+                        "error_m_median": float(np.median(err_f)),
+                        "error_m_max": float(np.max(err_f))}
+    out["coarse_plus_refine"] = {
+        "ms_per_step": float(ms_c.mean()),
+        "points_per_frame": 7500 + REFINE_LEVELS * offs.shape[0],
+        "levels": REFINE_LEVELS, "stencil": "5 x 5 x 5", "first_step_m": REFINE_STEP,
+        "last_step_m": REFINE_STEP * REFINE_SHRINK ** (REFINE_LEVELS - 1),
+        "coarse_only_error_m_median": float(np.median(err_0)),
+        "error_m_median": float(np.median(err_c)), "error_m_max": float(np.max(err_c))}
+    out["speedup"] = float(ms_f.mean() / ms_c.mean())
     return out
 
 

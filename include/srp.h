@@ -269,8 +269,9 @@ SRP_API srp_status srp_gcc_samples_static(int32_t M, int32_t K, int32_t n_aux,
 /* Device error flags raised since the previous poll, read on stream s
  * (which is synchronised) and cleared.  Returns SRP_ERR_TIMEOUT if a
  * bounded wait inside a tensor-core kernel gave up (the kernel then
- * returned early and its outputs are invalid), else SRP_OK.  srp_map_host
- * polls by itself.                                                        */
+ * returned early and its outputs are invalid), SRP_ERR_INVALID_ARG if
+ * srp_refine met a centre index outside [0, J), else SRP_OK.
+ * srp_map_host polls by itself.                                           */
 SRP_API srp_status srp_poll_device_status(srp_handle h, srp_stream_t s);
 
 /* Per-stage timing: when enabled, srp_map records CUDA events around each
@@ -285,6 +286,64 @@ SRP_API srp_status srp_last_launch_count(srp_handle h, int32_t *n);
 
 /* Release every device and host resource of the plan.  NULL is a no-op.  */
 SRP_API srp_status srp_destroy(srp_handle h);
+
+/* ------------------------------------------------------------------------
+ * Coarse-to-fine search on the interpolated map.  Sec. 3.3 notes that the
+ * interpolation cost R_int = N/K falls far lower when, instead of every
+ * candidate of a fine grid, only points near a coarse maximiser are
+ * evaluated (a refinement the paper leaves outside its scope).  A refiner
+ * evaluates the approximation of Eq. SRPapprox, summed over pairs as in
+ * Eq. SRP_T_IFT, at arbitrary points, from the GCC samples of its plan's
+ * last map:
+ *   level 0 evaluates the points c + o_f (f < F) around the frame's centre c,
+ *   level v evaluates c_v + shrink^v o_f around the best point c_v of level
+ *   v - 1 (the first maximiser: the largest value, the lowest f),
+ * and the best point of the last level is the result.  On a direction grid
+ * (SRP_GRID_DIRECTIONS) every displaced point is normalised back onto the
+ * unit sphere.  TDOAs are computed from the geometry (Eq. Deltat_i or
+ * Eq. Deltat_i_spher) in FP32, relative to the microphones' centroid and
+ * with the distance difference in a form without cancellation, not
+ * quantised like the plan's table; the centres are kept in FP64; the
+ * samples are read in the precision the map used.  Nyquist plans only.
+ * ------------------------------------------------------------------------ */
+typedef struct srp_refiner_s *srp_refiner;
+
+typedef struct {
+    int32_t n_offsets;      /* F in [1, 1024]: points per level */
+    const double *offsets;  /* host [F][3] displacements o_f of level 0 (metres on a point
+                               grid, unit-vector components on a direction grid); copied */
+    int32_t levels;         /* in [1, 64] */
+    double shrink;          /* in (0, 1]: level v scales the displacements by shrink^v */
+    int32_t keep_grid;      /* 1: copy the plan's grid to the device so that srp_refine
+                               can take centres as candidate indices (e.g. the argmax of
+                               srp_map); 0: centres are given as coordinates */
+} srp_refine_desc;
+
+/* Build a refiner for plan h.  d must be the descriptor h was built from
+ * (its geometry is read again: microphones, and the grid with keep_grid);
+ * a descriptor that differs in M, J, K, N_aux, fs, c, grid kind or lag
+ * counts is SRP_ERR_INVALID_ARG, a conventional plan SRP_ERR_UNSUPPORTED.
+ * Allocates 24 (M + F) bytes on the plan's device, plus 24 J with
+ * keep_grid.  h must outlive the refiner.  Blocking.                      */
+SRP_API srp_status srp_refiner_create(srp_handle h, const srp_plan_desc *d,
+                                      const srp_refine_desc *r, srp_refiner *out);
+
+/* Refine frames 0 .. L-1 of the plan's last srp_map, srp_map_host or
+ * srp_map_host_async call (not srp_map_batch, whose samples live in the
+ * batch), enqueued on s after that call and before the plan's next map.
+ * L in [0, frames of that call].  Centres: exactly one of d_argmax (device
+ * [L] candidate indices; needs keep_grid) and d_centres (device [L][3]
+ * coordinates).  Outputs (device): d_best_xyz [L][3] the best point of the
+ * last level, d_best_val [L] its value, d_values [L][F] every value of the
+ * last level, or NULL.  A centre index outside [0, J) makes that frame's
+ * outputs NaN and is reported by srp_poll_device_status as
+ * SRP_ERR_INVALID_ARG.  One kernel launch, asynchronous.                 */
+SRP_API srp_status srp_refine(srp_refiner r, int32_t L, const int32_t *d_argmax,
+                              const double *d_centres, double *d_best_xyz, float *d_best_val,
+                              float *d_values, srp_stream_t s);
+
+/* Release the refiner's device tables.  NULL is a no-op.                  */
+SRP_API srp_status srp_refiner_destroy(srp_refiner r);
 
 /* ------------------------------------------------------------------------
  * Batched uneven instances.  The paper maps one array at a time; a batch

@@ -195,6 +195,39 @@ def nyquist(xi, Nq, n_aux: int, x):
     return out
 
 
+def refine(xi, mic_xyz, fs, c, Nq, n_aux: int, centres, offsets, levels: int, shrink: float,
+           far_field: bool = False):
+    """Coarse-to-fine search on the approximation (the refinement Sec. 3.3
+    leaves outside the paper's scope), step by step per frame l: level v
+    evaluates SRP_appr (Eq. SRPapprox summed over pairs) at the points
+    c_v + shrink^v o_f, normalised onto the unit sphere on a direction grid;
+    c_0 is the frame's centre and c_{v+1} the first maximiser of level v.
+    Returns (best point [L][3], its value [L], values of the last level
+    [L][F])."""
+    xi = np.atleast_2d(np.asarray(xi, np.float64))
+    centres = np.asarray(centres, np.float64).reshape(-1, 3)
+    offsets = np.asarray(offsets, np.float64).reshape(-1, 3)
+    L = xi.shape[0]
+    best = np.zeros((L, 3))
+    best_val = np.zeros(L)
+    last = np.zeros((L, offsets.shape[0]))
+    for l in range(L):
+        centre = centres[l].copy()
+        scale = 1.0
+        for v in range(levels):
+            pts = centre[None, :] + scale * offsets
+            if far_field:
+                nrm = np.sqrt(np.sum(pts ** 2, axis=1))
+                pts = np.where(nrm[:, None] > 0.0, pts / np.where(nrm > 0.0, nrm, 1.0)[:, None],
+                               centre[None, :])
+            vals = nyquist(xi[l:l + 1], Nq, n_aux, tdoa(mic_xyz, pts, fs, c, far_field))[0]
+            (k,), (val,) = argmax(vals[None, :])
+            centre = pts[k].copy()
+            scale *= shrink
+        best[l], best_val[l], last[l] = centre, val, vals
+    return best, best_val, last
+
+
 def argmax(maps):
     """First maximiser and its value per frame (Sec. 2.2)."""
     maps = _c64(maps)

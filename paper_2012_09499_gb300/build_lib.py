@@ -49,7 +49,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     """Compile and link libsrp.so; returns its path.  Skips work when the
     library is newer than every source and header."""
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    deps = srcs + glob.glob(os.path.join(CSRC, "*.h")) + \
+    deps = srcs + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
     if (not force and os.path.exists(LIB) and
             os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in deps)):

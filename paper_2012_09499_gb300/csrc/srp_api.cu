@@ -454,10 +454,13 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     ++launches;
     record(h, 4, s);
     h->last_launches = launches;
+    h->last_L = L;
     return SRP_OK;
 }
 
 }  // namespace
+
+srp_status describe_layout(const srp_plan_desc *d, Layout &lay) { return make_layout(d, lay); }
 
 void set_error(const std::string &msg) { g_err = msg; }
 
@@ -533,6 +536,9 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     h->input_kind = d->input_kind;
     h->weighting = d->weighting;
     h->host_io = d->host_io;
+    h->fs = d->fs;
+    h->c = d->c;
+    h->grid_kind = d->grid_kind;
     const Layout &L = h->lay;
     auto bail = [&](srp_status s) {
         release(h);
@@ -779,6 +785,7 @@ srp_status srp_poll_device_status(srp_handle h, srp_stream_t s) {
     SRP_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), cs), "clear device status");
     SRP_CUDA(cudaStreamSynchronize(cs), "synchronise stream");
     if (flags & 1) return fail(SRP_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel gave up");
+    if (flags & 2) return fail(SRP_ERR_INVALID_ARG, "a refinement centre index was outside [0, J)");
     return SRP_OK;
 }
 

@@ -61,6 +61,9 @@ struct srp_plan_s {
     srp_input_kind input_kind = SRP_IN_STFT;
     srp_weighting weighting = SRP_WEIGHT_PHAT;
     int host_io = 0;
+    double fs = 0.0, c = 0.0;      // sampling rate and speed of sound of the descriptor
+    srp_grid_kind grid_kind = SRP_GRID_POINTS;
+    int last_L = 0;                // frames of the last map whose GCC samples the plan holds
     srp::Layout lay;
     // device tables (owned)
     int2 *d_pairs = nullptr;       // [Q] (m, m')
@@ -98,6 +101,9 @@ struct srp_plan_s {
 };
 
 namespace srp {
+
+// Validate a descriptor and compute its layout (host only), as srp_plan does.
+srp_status describe_layout(const srp_plan_desc *d, Layout &lay);
 
 void set_error(const std::string &msg);
 // Record msg (or the CUDA error text) for srp_last_error_message; return the status.

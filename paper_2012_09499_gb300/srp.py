@@ -63,6 +63,13 @@ class srp_complexity(ctypes.Structure):
     ]
 
 
+class srp_refine_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_offsets", ctypes.c_int32), ("offsets", ctypes.POINTER(ctypes.c_double)),
+        ("levels", ctypes.c_int32), ("shrink", ctypes.c_double), ("keep_grid", ctypes.c_int32),
+    ]
+
+
 class srp_batch_tiles(ctypes.Structure):
     _fields_ = [("frames_per_tile", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("operand_a", ctypes.c_int32),
@@ -128,6 +135,9 @@ def lib():
             "srp_last_launch_count": [vp, ctypes.POINTER(i32)],
             "srp_destroy": [vp],
             "srp_poll_device_status": [vp, vp],
+            "srp_refiner_create": [vp, dp, ctypes.POINTER(srp_refine_desc), ctypes.POINTER(vp)],
+            "srp_refine": [vp, i32, vp, vp, vp, vp, vp, vp],
+            "srp_refiner_destroy": [vp],
             "srp_batch_create": [vp, i32, vp, ctypes.POINTER(vp)],
             "srp_map_batch": [vp, vp, vp, vp, vp, vp, vp],
             "srp_batch_tune": [vp, vp, vp, vp, vp, vp, vp],
@@ -334,6 +344,47 @@ class Plan:
     def close(self):
         if self.handle is not None:
             srp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Refiner:
+    """Coarse-to-fine search around per-frame centres on a Nyquist Plan (see
+    srp_refine): offsets [F][3], levels, shrink per level; keep_grid lets
+    refine() take the plan's argmax as centres."""
+
+    def __init__(self, plan, offsets, levels=1, shrink=0.5, keep_grid=True):
+        self.plan = plan
+        self.offsets = np.ascontiguousarray(offsets, np.float64).reshape(-1, 3)
+        d = srp_refine_desc(self.offsets.shape[0],
+                            self.offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            int(levels), float(shrink), 1 if keep_grid else 0)
+        h = ctypes.c_void_p()
+        _check(lib().srp_refiner_create(plan.handle, ctypes.byref(plan.desc), ctypes.byref(d),
+                                        ctypes.byref(h)), "srp_refiner_create")
+        self.handle = h
+
+    def refine(self, L, argmax=None, centres=None, values=False, stream=None):
+        """Returns (best_xyz [L][3] float64, best_val [L], values [L][F] or
+        None) as CUDA tensors; argmax: int32 [L] or centres: float64 [L][3]."""
+        import torch
+        dev = (argmax if argmax is not None else centres).device
+        xyz = torch.empty((L, 3), dtype=torch.float64, device=dev)
+        val = torch.empty(L, dtype=torch.float32, device=dev)
+        vals = (torch.empty((L, self.offsets.shape[0]), dtype=torch.float32, device=dev)
+                if values else None)
+        _check(lib().srp_refine(self.handle, int(L), _ptr(argmax), _ptr(centres), _ptr(xyz),
+                                _ptr(val), _ptr(vals), _stream(stream)), "srp_refine")
+        return xyz, val, vals
+
+    def close(self):
+        if self.handle is not None:
+            lib().srp_refiner_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

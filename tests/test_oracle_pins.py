@@ -97,6 +97,68 @@ def test_complexity_circle_closed_form():
         assert cx["N"] == 2.0 / 15.0 * (6 * f(r) + 6 * f(np.sqrt(3.0) * r) + 3 * f(2 * r)) + 5
 
 
+# --------------------------------------------------------------------------
+# coarse-to-fine refinement (oracle.refine)
+# --------------------------------------------------------------------------
+
+def test_refine_at_exact_sample_points():
+    """Where every pair's TDOA is an integer lag, Eq. SRPapprox returns the
+    GCC sample itself (sinc(0) = 1, sinc(k) = 0), so SRP_appr = sum_q xi_q(x_q).
+    A linear array along x with spacing c / fs and the far-field directions
+    +x and -x give x_q = m - m' and m' - m (Eq. Deltat_i_spher)."""
+    fs, c = 8192.0, 256.0
+    mic = np.array([[k / 32.0, 0.0, 0.0] for k in range(4)])  # spacing 1/32 m = c / fs
+    rng = np.random.default_rng(7)
+    psi = oracle.cross_spectra(_rand_cplx(rng, (3, 4, 33)))  # K = 64
+    Nq, _ = oracle.lag_counts(mic, fs, c)
+    assert Nq.tolist() == [1, 2, 3, 1, 2, 1]
+    xi = oracle.gcc_samples(psi, Nq, 1, 64)
+    m, mp = oracle.pairs(4)
+    offs = np.concatenate([[0], np.cumsum(2 * Nq + 3)[:-1]])
+    for sgn in (1, -1):
+        centres = np.tile([float(sgn), 0.0, 0.0], (3, 1))
+        best, val, last = oracle.refine(xi, mic, fs, c, Nq, 1, centres, np.zeros((1, 3)), 1, 0.5,
+                                        far_field=True)
+        lag = sgn * (m - mp)
+        expect = [sum(xi[l, offs[q] + lag[q] + Nq[q] + 1] for q in range(6)) for l in range(3)]
+        assert np.allclose(last[:, 0], expect, rtol=0.0, atol=1e-12)
+        assert np.array_equal(best, centres) and np.array_equal(val, last[:, 0])
+
+
+def _cube(h):
+    g = np.array([-1.0, 0.0, 1.0]) * h
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    return np.concatenate([np.zeros((1, 3)), pts[np.any(pts != 0.0, axis=1)]])  # 0 first
+
+
+def test_refine_level_invariants():
+    """Facts the search fixes: with the zero displacement in the stencil the
+    best value never falls from one level to the next; on a direction grid
+    every point has unit norm; with displacements {0, h e_x} and shrink 1/2
+    the result after V levels is c + b h 2^-(V-1) e_x with integer b in
+    [0, 2^V - 1]."""
+    rng = np.random.default_rng(11)
+    mic = rng.uniform(-0.15, 0.15, (5, 3))
+    fs, c, K = 16000.0, 343.0, 256
+    Nq, _ = oracle.lag_counts(mic, fs, c)
+    xi = oracle.gcc_samples(oracle.cross_spectra(_rand_cplx(rng, (2, 5, K // 2 + 1))), Nq, 2, K)
+    centres = rng.uniform(-1.0, 1.0, (2, 3))
+    vals = [oracle.refine(xi, mic, fs, c, Nq, 2, centres, _cube(0.1), v, 0.5)[1]
+            for v in range(1, 5)]
+    for a, b in zip(vals, vals[1:]):
+        assert np.all(b >= a)
+    dirs = centres / np.linalg.norm(centres, axis=1, keepdims=True)
+    best, _, _ = oracle.refine(xi, mic, fs, c, Nq, 2, dirs, _cube(0.2), 3, 0.5, far_field=True)
+    assert np.allclose(np.linalg.norm(best, axis=1), 1.0, rtol=0.0, atol=1e-12)
+    h, V = 0.08, 5
+    best, _, _ = oracle.refine(xi, mic, fs, c, Nq, 2, centres, np.array([[0, 0, 0], [h, 0, 0]]),
+                               V, 0.5)
+    d = best - centres
+    assert np.all(d[:, 1:] == 0.0)
+    b = d[:, 0] / h * 2 ** (V - 1)
+    assert np.allclose(b, np.round(b), atol=1e-9) and np.all((b > -0.5) & (b < 2 ** V - 0.5))
+
+
 def test_lag_count_exact_integer_boundary():
     # d = 0.5 m, c = 256 m/s, fs = 8192 Hz: d fs / c = 16 exactly in binary.
     mic = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])

@@ -1,0 +1,175 @@
+"""Coarse-to-fine search (srp_refine) through the C ABI against the FP64
+oracle's refinement (oracle.refine): the values of one level at every
+stencil point within the map tolerance of each precision, the point found
+after several levels on point and direction grids, and the argument and
+centre-index checks."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle
+from paper_2012_09499_gb300 import build_lib, srp, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-4, "bf16": 1e-2, "fp16": 1e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build_lib.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def cube(h, n):
+    """n^3 displacements of a cube of step h, the zero displacement first."""
+    g = (np.arange(n) - (n - 1) / 2.0) * h
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    return np.concatenate([np.zeros((1, 3)), pts[np.any(pts != 0.0, axis=1)]])
+
+
+def coarse_room(seed, L):
+    """One source in the 6 x 7 x 3.5 m room, eight microphones in a 0.5 m
+    cube, a coarse 3D grid of about 2000 cell centres (0.42 m)."""
+    return synth.uneven_instance(seed, (2000, 2001), L, dims=3, M=8, K=1024, aperture=0.5)
+
+
+def oracle_xi(cfg, n_aux=2):
+    Nq, _ = oracle.lag_counts(cfg["mic"], cfg["fs"], cfg["c"])
+    xi = oracle.gcc_samples(oracle.cross_spectra(cfg["Y"]), Nq, n_aux, cfg["K"])
+    return xi, Nq
+
+
+def coarse_peak(cfg, xi, Nq, n_aux=2):
+    x = oracle.tdoa(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["far_field"])
+    return np.abs(oracle.nyquist(xi, Nq, n_aux, x)).max(axis=1)
+
+
+def plan_for(cfg, precision="fp32", engine="auto"):
+    return srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], mode="nyquist",
+                    n_aux=2, precision=precision, engine=engine, far_field=cfg["far_field"],
+                    max_frames=cfg["L"])
+
+
+@pytest.mark.parametrize("precision,engine", [("fp32", "auto"), ("bf16", "auto"),
+                                              ("fp16", "auto"), ("fp32", "cuda_cores")])
+def test_one_level_values_match_oracle(precision, engine):
+    cfg = coarse_room(1, 8)
+    plan = plan_for(cfg, precision, engine)
+    assert plan.info.tensor_cores == (0 if engine == "cuda_cores" else 1)
+    _, am, _ = plan.map(torch.from_numpy(cfg["Y"]).cuda())
+    spacing = float(np.min(np.diff(np.unique(cfg["grid"][:, 0]))))
+    offs = cube(spacing / 4.0, 5)  # 125 points within half a cell
+    ref = srp.Refiner(plan, offs, levels=1)
+    xyz, val, vals = ref.refine(8, argmax=am, values=True)
+    centres = cfg["grid"][am.cpu().numpy()]
+    # the same centres as coordinates give the same outputs
+    xyz2, val2, vals2 = ref.refine(8, centres=torch.from_numpy(centres).cuda(), values=True)
+    torch.cuda.synchronize()
+    srp.srp_poll_device_status(plan.handle)
+    xyz, val, vals = xyz.cpu().numpy(), val.cpu().numpy(), vals.cpu().numpy()
+    assert np.array_equal(xyz, xyz2.cpu().numpy()) and np.array_equal(vals, vals2.cpu().numpy())
+    xi, Nq = oracle_xi(cfg)
+    _, _, rlast = oracle.refine(xi, cfg["mic"], cfg["fs"], cfg["c"], Nq, 2, centres, offs, 1, 0.5)
+    pk = coarse_peak(cfg, xi, Nq)
+    err = np.abs(vals - rlast).max(axis=1)
+    assert np.all(err <= TOL[precision] * pk), (err / pk).max()
+    # the result is the first maximiser of the level's own values
+    k = np.argmax(vals, axis=1)
+    assert np.array_equal(val, vals[np.arange(8), k])
+    assert np.allclose(xyz, centres + offs[k], rtol=0.0, atol=1e-12)
+    rk = np.argmax(rlast, axis=1)
+    for l in np.nonzero(k != rk)[0]:  # documented ties only
+        assert rlast[l, rk[l]] - rlast[l, k[l]] <= 2 * TOL[precision] * pk[l]
+    ref.close()
+    plan.close()
+
+
+def multilevel_case(cfg, offs, levels, shrink):
+    plan = plan_for(cfg)
+    _, am, _ = plan.map(torch.from_numpy(cfg["Y"]).cuda())
+    ref = srp.Refiner(plan, offs, levels=levels, shrink=shrink)
+    xyz, val, _ = ref.refine(cfg["L"], argmax=am)
+    torch.cuda.synchronize()
+    srp.srp_poll_device_status(plan.handle)
+    centres = cfg["grid"][am.cpu().numpy()]
+    xyz, val = xyz.cpu().numpy(), val.cpu().numpy()
+    ref.close()
+    plan.close()
+    xi, Nq = oracle_xi(cfg)
+    rb, rv, _ = oracle.refine(xi, cfg["mic"], cfg["fs"], cfg["c"], Nq, 2, centres, offs, levels,
+                              shrink, far_field=cfg["far_field"])
+    pk = coarse_peak(cfg, xi, Nq)
+    # the GPU's value is the oracle's SRP_appr at the GPU's point
+    x = oracle.tdoa(cfg["mic"], xyz, cfg["fs"], cfg["c"], cfg["far_field"])
+    at_gpu = np.array([oracle.nyquist(xi[l:l + 1], Nq, 2, x[l:l + 1])[0, 0]
+                       for l in range(cfg["L"])])
+    assert np.all(np.abs(val - at_gpu) <= TOL["fp32"] * pk)
+    same = np.all(np.abs(xyz - rb) <= 1e-9, axis=1)
+    # a near tie at some level may lead the two searches apart; then the GPU's
+    # point must still be (almost) as good as the oracle's
+    assert np.mean(same) >= 0.9, np.mean(same)
+    assert np.all(at_gpu[~same] >= rv[~same] - 2 * TOL["fp32"] * pk[~same])
+    return xyz, rb
+
+
+def test_multilevel_search_point_grid():
+    cfg = coarse_room(2, 16)
+    spacing = float(np.min(np.diff(np.unique(cfg["grid"][:, 0]))))
+    multilevel_case(cfg, cube(spacing / 2.0, 5), 4, 0.5)
+
+
+def test_multilevel_search_direction_grid():
+    cfg = synth.paper_circle_setup(7, L=16, step_deg=10.0)
+    xyz, _ = multilevel_case(cfg, cube(np.radians(5.0), 5), 4, 0.5)
+    assert np.allclose(np.linalg.norm(xyz, axis=1), 1.0, atol=1e-12)
+
+
+def test_refiner_arguments_and_bad_centres():
+    cfg = coarse_room(3, 4)
+    offs = cube(0.1, 3)
+    conv = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], mode="conventional",
+                    max_frames=4)
+    with pytest.raises(srp.SrpError) as e:
+        srp.Refiner(conv, offs)
+    assert e.value.status == srp.SRP_ERR_UNSUPPORTED
+    conv.close()
+    plan = plan_for(cfg)
+    # a descriptor that is not the plan's
+    d, keep = srp.make_desc(cfg["mic"], cfg["grid"], 2.0 * cfg["fs"], cfg["c"], cfg["K"],
+                            max_frames=4)
+    rd = srp.srp_refine_desc(offs.shape[0], offs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             1, 0.5, 1)
+    h = ctypes.c_void_p()
+    assert srp.lib().srp_refiner_create(plan.handle, ctypes.byref(d), ctypes.byref(rd),
+                                        ctypes.byref(h)) == srp.SRP_ERR_INVALID_ARG
+    for kw in ({"levels": 0}, {"shrink": 0.0}, {"shrink": 1.5}):
+        with pytest.raises(srp.SrpError):
+            srp.Refiner(plan, offs, **kw)
+    with pytest.raises(srp.SrpError):
+        srp.Refiner(plan, np.zeros((0, 3)))
+    ref = srp.Refiner(plan, offs, keep_grid=False)
+    am = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(srp.SrpError):  # no map has run on the plan yet
+        ref.refine(4, centres=torch.zeros((4, 3), dtype=torch.float64, device="cuda"))
+    plan.map(torch.from_numpy(cfg["Y"]).cuda(), L=3)
+    with pytest.raises(srp.SrpError):  # centre indices need keep_grid
+        ref.refine(3, argmax=am)
+    with pytest.raises(srp.SrpError):  # more frames than the last map
+        ref.refine(4, centres=torch.zeros((4, 3), dtype=torch.float64, device="cuda"))
+    ref.close()
+    ref = srp.Refiner(plan, offs)
+    bad = torch.tensor([0, -1, int(cfg["grid"].shape[0])], dtype=torch.int32, device="cuda")
+    xyz, val, vals = ref.refine(3, argmax=bad, values=True)
+    torch.cuda.synchronize()
+    with pytest.raises(srp.SrpError) as e:
+        srp.srp_poll_device_status(plan.handle)
+    assert e.value.status == srp.SRP_ERR_INVALID_ARG
+    val = val.cpu().numpy()
+    assert np.isfinite(val[0]) and np.all(np.isnan(val[1:]))
+    assert np.all(np.isnan(xyz.cpu().numpy()[1:])) and np.all(np.isnan(vals.cpu().numpy()[1:]))
+    srp.srp_poll_device_status(plan.handle)  # cleared by the previous poll
+    ref.close()
+    plan.close()
