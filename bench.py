@@ -488,6 +488,8 @@ def bench_batched(args, flush, stream):
             "stage_ms": stage, "gpu_launches_per_step": int(info.launches),
             "tiles": {"frames_per_item": info.tiles.frames_per_tile,
                       "stages": info.tiles.stages, "ctas_per_sm": info.tiles.ctas_per_sm,
+                      "operand_a": "tmem" if info.tiles.operand_a == 1 else "smem",
+                      "accumulators": info.tiles.accumulators,
                       "tuned_ms": float(info.tuned_ms)},
             "work_items": int(info.items), "persistent_ctas": int(info.ctas),
             "resident_weight_bytes": int(sum(p.info.weight_bytes for p in plans)),
