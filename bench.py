@@ -310,6 +310,18 @@ def bench_ours(args):
         srp.srp_map_host(ny.handle, h_in[k % 4], L, h_maps[0], h_am[0], h_pk[0], stream)
     e2e_sync_s = reduce_max((time.perf_counter() - t0) / e2e_steps, world,
                             dev if world > 1 else None)
+    # the same pipeline returning only each frame's maximiser and peak
+    # (localisation), without the maps
+    for k in range(args.warmup):
+        srp.srp_map_host_async(ny.handle, h_in[k % 4], L, None, h_am[k % 2], h_pk[k % 2], stream)
+    srp.srp_map_host_wait(ny.handle)
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        srp.srp_map_host_async(ny.handle, h_in[k % 4], L, None, h_am[k % 2], h_pk[k % 2], stream)
+    srp.srp_map_host_wait(ny.handle)
+    e2e_loc_s = reduce_max((time.perf_counter() - t0) / e2e_steps, world,
+                           dev if world > 1 else None)
 
     cells = J * Q * L
     ny_ms = reduce_max(res["nyquist"]["ms"].mean(), world, dev if world > 1 else None)
@@ -402,7 +414,12 @@ def bench_ours(args):
                        "step's input copied in and its maps, argmax and peak copied back, "
                        "overlapped with the neighbouring steps' maps)",
                 "synchronous": {"value": world * cells / e2e_sync_s, "ms_per_step": e2e_sync_s * 1e3,
-                                "api": "srp_map_host, one step at a time"}},
+                                "api": "srp_map_host, one step at a time"},
+                "localisation_only": {
+                    "value": world * cells / e2e_loc_s, "ms_per_step": e2e_loc_s * 1e3,
+                    "d2h_bytes_per_step": int(L * 8),
+                    "api": "srp_map_host_async with h_maps = NULL: every step's input copied "
+                           "in, its argmax and peak copied back, the maps left on the device"}},
         "gpu_launches": int(res["nyquist"]["launches"]),
         "clocks": clocks,
         "cpu_baseline": cpu,

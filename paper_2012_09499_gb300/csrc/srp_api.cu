@@ -134,8 +134,9 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         for (int q = 0; q < lay.Q; ++q) {
             lay.offc.push_back((int32_t)sc);
             sc += round_up(tc_span(d, lay, q), kLagPad);
-            if (tc_span(d, lay, q) > 16) lay.par1_used = 1;  // a chunk with 2+ MMA steps
         }
+        // the second accumulator takes every other 16-slot step of the tile
+        lay.par1_used = lay.mma_steps >= 2 ? 1 : 0;
         lay.Sc = (int)sc;
         lay.n_chunks = (int)(sc / kLagPad);
         lay.N_tc = interp_tc_frames_per_cta(d->max_frames);

@@ -265,7 +265,8 @@ __device__ __forceinline__ void sync_128() { asm volatile("bar.sync 1, 128;" :::
 // The persistent contraction.  Warps 0-3 generate operand A (one candidate
 // row per thread) and run the epilogue of the previous item after the
 // operands of the current one; warp 4 issues the TMA loads of B; warps 5-6
-// issue the MMAs by 16-slot step parity into two accumulators (or warp 5
+// issue the MMAs into two accumulators by the parity of the item's running
+// 16-slot step count (or warp 5
 // alone into one, mma_warps = 1).  TMEM holds two such accumulator sets (item
 // parity), columns [b W N, b W N + W N) for W = mma_warps.
 // ---------------------------------------------------------------------------
@@ -608,6 +609,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                 tc_fence_after();
                 const uint32_t dt = tmem + (uint32_t)((b * nw + par) * N);
                 uint32_t acc = 0;  // the item's first MMA overwrites the accumulator
+                int g0 = 0;        // 16-slot steps of the item's earlier chunks
                 const int n_chunks = I.n_chunks;
                 const int4 *ctab = I.ctab;
                 const bool resident = !kConv && !kTm && I.w != nullptr;
@@ -624,7 +626,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                     const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
                     const int nk = __ldg(&ctab[c]).w;
                     const bool streamed = resident && __ldg(&I.woff[c]) >= 0;
-                    for (int kk = par; kk < nk; kk += nw) {
+                    // steps alternate over the nw accumulators by the running
+                    // step count of the item (balanced chains)
+                    const int kk0 = (par + g0) % nw;
+                    g0 += nk;
+                    for (int kk = kk0; kk < nk; kk += nw) {
                         const uint64_t adv = (uint64_t)(kk * 2);
                         const uint32_t ac = (uint32_t)(kk * 8);
                         if (kTm) {

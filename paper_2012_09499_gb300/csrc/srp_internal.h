@@ -35,7 +35,8 @@ struct Layout {
     int L_max = 0, L_pad = 0, n_tiles = 0;
     std::vector<int32_t> Nq, off, pm, pmp;  // per pair
     // tensor-core lag layout: pair q owns ceil(N'_q / 64) chunks of 64 slots
-    int Sc = 0, n_chunks = 0, N_tc = 0, par1_used = 0;
+    int Sc = 0, n_chunks = 0, N_tc = 0;
+    int par1_used = 0;  // the tile has two or more 16-slot MMA steps (both accumulators written)
     int mma_steps = 0;   // tensor-core plans: 16-slot MMA steps per tile over all pairs
     int tile_steps = 0;  // resident interpolation matrix: 16-slot steps per tile (0: generated)
     int total_steps = 0; // 16-slot steps holding lags, per tile, of all pairs (resident plans)

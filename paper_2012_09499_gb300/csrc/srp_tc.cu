@@ -134,7 +134,7 @@ struct TcArgs {
     int *status;
     int vec_maps;           // maps rows are 8-byte aligned (float2 stores)
     uint32_t a_col0;        // operand A in TMEM: first column of the A stages
-    int par1_used;          // some chunk has two or more 16-lag steps
+    int par1_used;          // the tile has two or more 16-lag steps: accumulator 1 is written
     const uint4 *w;         // resident operand A (kW): the plan's interpolation matrix
     const int32_t *woff;    // [n_chunks] first 16-slot step of chunk c within a tile's block
     int tile_steps;         // 16-slot steps per 128-candidate tile
@@ -454,13 +454,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
         }
     } else {
         // ---------------- MMA issue: two warps, by 16-lag step parity ----------------
-        // One 128 x N x 16 MMA is small at N = 64, so the steps are spread over
-        // two accumulators (TMEM columns [0, N) and [N, 2N)), each fed by its
-        // own issuing warp; the epilogue adds them.
+        // One 128 x N x 16 MMA is small at N = 64, and MMAs into one accumulator
+        // form a dependent chain, so the steps are spread over two accumulators
+        // (TMEM columns [0, N) and [N, 2N)), each fed by its own issuing warp;
+        // the epilogue adds them.  The parity is that of the running step count
+        // over the whole tile, which balances the two chains also when every
+        // chunk holds an odd number of steps.
         const int par = warp - kMmaWarp0;
         if (lane == 0) {
             const uint32_t dt = tmem + (uint32_t)(par * a.N);
             uint32_t acc = 0;  // the first MMA into the accumulator overwrites it
+            int g0 = 0;        // 16-lag steps of the earlier chunks
             for (int c = 0; c < a.n_chunks; ++c) {
                 const int st = c % a.stages;
                 const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
@@ -471,7 +475,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                 const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
                 const int nk = __ldg(&a.ctab[c]).w;  // 16-lag steps holding lags of the pair
                 const bool streamed = kW && __ldg(&a.woff[c]) >= 0;
-                for (int kk = par; kk < nk; kk += 2) {
+                const int kk0 = (par + g0) & 1;  // this warp's first step of the chunk
+                g0 += nk;
+                for (int kk = kk0; kk < nk; kk += 2) {
                     const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
                     const uint32_t ac = (uint32_t)(kk * 8);   // 16 values in 8 TMEM columns
                     if (kTm) {
