@@ -173,3 +173,28 @@ def test_refiner_arguments_and_bad_centres():
     srp.srp_poll_device_status(plan.handle)  # cleared by the previous poll
     ref.close()
     plan.close()
+
+
+def test_large_array_reads_samples_from_global_memory():
+    """40 microphones (780 pairs) on a 1 m aperture: the frame's samples
+    (780 x 2(N_q + N_aux) + 1) exceed the 200 KB staged in shared memory, so
+    the kernel reads them from global memory; values still match the oracle."""
+    cfg = synth.uneven_instance(9, (400, 401), 2, dims=2, M=40, K=512, aperture=1.0)
+    Nq, _ = oracle.lag_counts(cfg["mic"], cfg["fs"], cfg["c"])
+    span = int(2 * (Nq.max() + 2) + 1) | 1
+    assert 4 * len(Nq) * span > 200 * 1024
+    plan = plan_for(cfg)
+    _, am, _ = plan.map(torch.from_numpy(cfg["Y"]).cuda())
+    offs = cube(0.05, 3)
+    ref = srp.Refiner(plan, offs, levels=1)
+    _, _, vals = ref.refine(2, argmax=am, values=True)
+    torch.cuda.synchronize()
+    srp.srp_poll_device_status(plan.handle)
+    centres = cfg["grid"][am.cpu().numpy()]
+    xi, Nq = oracle_xi(cfg)
+    _, _, rlast = oracle.refine(xi, cfg["mic"], cfg["fs"], cfg["c"], Nq, 2, centres, offs, 1, 0.5)
+    pk = coarse_peak(cfg, xi, Nq)
+    err = np.abs(vals.cpu().numpy() - rlast).max(axis=1)
+    assert np.all(err <= TOL["fp32"] * pk), (err / pk).max()
+    ref.close()
+    plan.close()
