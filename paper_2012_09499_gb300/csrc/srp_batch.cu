@@ -613,19 +613,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_const
                 const int n_chunks = I.n_chunks;
                 const int4 *ctab = I.ctab;
                 const bool resident = !kConv && !kTm && I.w != nullptr;
+                // the next chunk's table entry is loaded a chunk ahead
+                int nk_next = __ldg(&ctab[0]).w;
+                bool streamed_next = resident && __ldg(&I.woff[0]) >= 0;
                 for (int c = 0; c < n_chunks; ++c, ++g) {
                     const int st = g % a.stages;
                     const uint32_t ph = (uint32_t)(g / a.stages) & 1u;
-                    if (!mbar_wait(full_bar(st), ph, abort_flag, a.status)) {
+                    const int nk = nk_next;
+                    const bool streamed = streamed_next;
+                    if (c + 1 < n_chunks) {
+                        nk_next = __ldg(&ctab[c + 1]).w;
+                        streamed_next = resident && __ldg(&I.woff[c + 1]) >= 0;
+                    }
+                    const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
+                    const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
+                    const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
+                    if (!mbar_try_wait(full_bar(st), ph) &&
+                        !mbar_wait(full_bar(st), ph, abort_flag, a.status)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
-                    const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
-                    const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
-                    const int nk = __ldg(&ctab[c]).w;
-                    const bool streamed = resident && __ldg(&I.woff[c]) >= 0;
                     // steps alternate over the nw accumulators by the running
                     // step count of the item (balanced chains)
                     const int kk0 = (par + g0) % nw;

@@ -465,16 +465,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             const uint32_t dt = tmem + (uint32_t)(par * a.N);
             uint32_t acc = 0;  // the first MMA into the accumulator overwrites it
             int g0 = 0;        // 16-lag steps of the earlier chunks
+            // the chunk table entry of the next chunk is loaded a chunk ahead,
+            // so that its latency overlaps the wait instead of delaying the MMAs
+            int nk_next = __ldg(&a.ctab[0]).w;
+            bool streamed_next = kW && __ldg(&a.woff[0]) >= 0;
             for (int c = 0; c < a.n_chunks; ++c) {
                 const int st = c % a.stages;
                 const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
-                if (!mbar_wait(full_bar(st), ph, abort_flag, a.status)) break;
-                tc_fence_after();
+                const int nk = nk_next;  // 16-lag steps holding lags of the pair
+                const bool streamed = streamed_next;
+                if (c + 1 < a.n_chunks) {
+                    nk_next = __ldg(&a.ctab[c + 1]).w;
+                    streamed_next = kW && __ldg(&a.woff[c + 1]) >= 0;
+                }
                 const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
                 const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
                 const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
-                const int nk = __ldg(&a.ctab[c]).w;  // 16-lag steps holding lags of the pair
-                const bool streamed = kW && __ldg(&a.woff[c]) >= 0;
+                if (!mbar_try_wait(full_bar(st), ph) &&
+                    !mbar_wait(full_bar(st), ph, abort_flag, a.status))
+                    break;
+                tc_fence_after();
                 const int kk0 = (par + g0) & 1;  // this warp's first step of the chunk
                 g0 += nk;
                 for (int kk = kk0; kk < nk; kk += 2) {
