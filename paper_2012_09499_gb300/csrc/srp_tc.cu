@@ -312,13 +312,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             }
             const float mc = x0f + __int_as_float(cur.y);  // Nyquist: x0 + nmax - first lag slot
             const int ng = cur.z;
-            if (c >= a.stages) mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status);
+            // the stage is reused once the MMAs of chunk c - stages completed; the
+            // weights are computed into registers before this wait and stored after
+            const uint32_t eb = empty_bar(st), eph = ph ^ 1u;
+            const bool reuse = c >= a.stages;
+            auto wait_free = [&]() {
+                if (reuse && !mbar_try_wait(eb, eph)) mbar_wait(eb, eph, abort_flag, a.status);
+            };
             // up to 64 weights, fully unrolled per group count
             const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
             const uint32_t d0 = kTm ? tmem + lane_base + a_tm(st, 0) : a_hi(st) + row;
             const uint32_t d1 = kTm ? tmem + lane_base + a_tm(st, 1) : 0u;
             if (kW && __ldg(&a.woff[c]) >= 0) {
                 // resident: the TMA warp brings this chunk's weights
+                wait_free();
             } else if (kConv) {
                 // exact seed e^{-j theta_k0} for the chunk's first bin k0 = cur.y
                 const int k0 = cur.y;
@@ -326,17 +333,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                 float sn, cs;
                 sincospif(fmaf((float)rk, two_k, (float)k0 * f * two_k), &sn, &cs);
                 switch (ng) {
-                    case 2: gen_steer<2, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
-                    case 4: gen_steer<4, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
-                    case 6: gen_steer<6, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
-                    default: gen_steer<8, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq); break;
+                    case 2: gen_steer<2, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq, 0u, nullptr, nullptr, wait_free); break;
+                    case 4: gen_steer<4, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq, 0u, nullptr, nullptr, wait_free); break;
+                    case 6: gen_steer<6, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq, 0u, nullptr, nullptr, wait_free); break;
+                    default: gen_steer<8, kSplit, kHalf, kTm>(d0, d1, sw, cs, -sn, wp, wq, 0u, nullptr, nullptr, wait_free); break;
                 }
             } else {
                 switch (ng) {
-                    case 2: gen_groups<2, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
-                    case 4: gen_groups<4, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
-                    case 6: gen_groups<6, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
-                    default: gen_groups<8, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp); break;
+                    case 2: gen_groups<2, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp, 0u, nullptr, nullptr, wait_free); break;
+                    case 4: gen_groups<4, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp, 0u, nullptr, nullptr, wait_free); break;
+                    case 6: gen_groups<6, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp, 0u, nullptr, nullptr, wait_free); break;
+                    default: gen_groups<8, kSplit, kHalf, kTm>(d0, d1, sw, f, mc, sp, 0u, nullptr, nullptr, wait_free); break;
                 }
             }
             if (kTm) {  // TMEM stores complete and ordered before the MMA's reads

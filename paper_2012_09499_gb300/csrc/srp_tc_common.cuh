@@ -308,19 +308,27 @@ __device__ __forceinline__ void store_group(uint32_t dst0, uint32_t dst1, uint32
 // Weights of NG groups of 8 lags for one candidate row of operand A:
 // w = sp / d with d = f + (mc - k) for lag slot k of the chunk, two lags per
 // reciprocal, stored by store_group (groups cc0 .. cc0 + NG - 1 of the row).
-// With kSplit, the low parts bf16(w - hi) are stored too.
-template <int NG, bool kSplit, bool kHalf, int kDst>
+// With kSplit, the low parts bf16(w - hi) are stored too.  Every weight of
+// the chunk is computed into registers first; wait() then runs before the
+// first store, so a generator that must wait for its stage to drain has its
+// arithmetic done by the time the stage is free.
+struct NoWait {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <int NG, bool kSplit, bool kHalf, int kDst, class Wait = NoWait>
 __device__ __forceinline__ void gen_groups(uint32_t dst0, uint32_t dst1, uint32_t sw, float f,
                                            float mc, float sp, uint32_t cc0 = 0,
-                                           uint4 *g0 = nullptr, uint4 *g1 = nullptr) {
+                                           uint4 *g0 = nullptr, uint4 *g1 = nullptr,
+                                           Wait wait = Wait()) {
     const uint64_t f2 = pk2(f, f);
     const uint64_t two = pk2(2.0f, 2.0f);
     // m2 = (mc - k - 1, mc - k): the second lag of a pair first, so that
     // (db, da) * rr = (w_a, w_b) comes out in lag order
     uint64_t m2 = pk2(mc - 1.0f, mc);
+    uint32_t hv[NG][4], lv[NG][4];
 #pragma unroll
     for (int cc = 0; cc < NG; ++cc) {
-        uint32_t hv[4], lv[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const uint64_t d2 = add2(f2, m2);  // (db, da), each rounded once
@@ -328,35 +336,41 @@ __device__ __forceinline__ void gen_groups(uint32_t dst0, uint32_t dst1, uint32_
             const float2 d = upk2(d2);
             const float rr = sp * rcp_approx(d.x * d.y);
             const float2 w = upk2(mul2(d2, pk2(rr, rr)));  // (w_a, w_b)
+            lv[cc][e] = 0u;
             if (kHalf) {
-                hv[e] = pack_f16(w.x, w.y);
+                hv[cc][e] = pack_f16(w.x, w.y);
             } else {
-                hv[e] = pack_bf16(w.x, w.y);
+                hv[cc][e] = pack_bf16(w.x, w.y);
                 if (kSplit) {
-                    const uint64_t h2 = pk2(__uint_as_float(hv[e] << 16),
-                                            __uint_as_float(hv[e] & 0xFFFF0000u));
+                    const uint64_t h2 = pk2(__uint_as_float(hv[cc][e] << 16),
+                                            __uint_as_float(hv[cc][e] & 0xFFFF0000u));
                     const float2 lo = upk2(sub2(pk2(w.x, w.y), h2));
-                    lv[e] = pack_bf16(lo.x, lo.y);
+                    lv[cc][e] = pack_bf16(lo.x, lo.y);
                 }
             }
         }
-        store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv, lv, g0, g1);
     }
+    wait();
+#pragma unroll
+    for (int cc = 0; cc < NG; ++cc)
+        store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv[cc], lv[cc], g0, g1);
 }
 
 // Steering weights of NG groups (4 bins each) for this thread's row of A: the
 // element pair (cos theta_k, -sin theta_k) of bins k0, k0 + 1, ..., i.e.
 // z = e^{-j theta_k}, starting from z0 and multiplied per bin by
 // w' = (p, q) = e^{-j 2 pi x / K}: z w' = (a p - b q, b p + a q) for z = (a, b).
-template <int NG, bool kSplit, bool kHalf, int kDst>
+// As in gen_groups, the chunk is computed into registers before wait().
+template <int NG, bool kSplit, bool kHalf, int kDst, class Wait = NoWait>
 __device__ __forceinline__ void gen_steer(uint32_t dst0, uint32_t dst1, uint32_t sw, float za,
                                           float zb, float p, float q, uint32_t cc0 = 0,
-                                          uint4 *g0 = nullptr, uint4 *g1 = nullptr) {
+                                          uint4 *g0 = nullptr, uint4 *g1 = nullptr,
+                                          Wait wait = Wait()) {
     uint64_t z = pk2(za, zb);
     const uint64_t pp = pk2(p, p), qq = pk2(-q, q);
+    uint32_t hv[NG][4], lv[NG][4];
 #pragma unroll
     for (int cc = 0; cc < NG; ++cc) {
-        uint32_t hv[4], lv[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float2 v = upk2(z);
@@ -364,20 +378,24 @@ __device__ __forceinline__ void gen_steer(uint32_t dst0, uint32_t dst1, uint32_t
             uint64_t zn;
             asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(zn) : "l"(pk2(v.y, v.x)), "l"(qq), "l"(t));
             z = zn;
+            lv[cc][e] = 0u;
             if (kHalf) {
-                hv[e] = pack_f16(v.x, v.y);
+                hv[cc][e] = pack_f16(v.x, v.y);
             } else {
-                hv[e] = pack_bf16(v.x, v.y);
+                hv[cc][e] = pack_bf16(v.x, v.y);
                 if (kSplit) {
-                    const uint64_t h2 = pk2(__uint_as_float(hv[e] << 16),
-                                            __uint_as_float(hv[e] & 0xFFFF0000u));
+                    const uint64_t h2 = pk2(__uint_as_float(hv[cc][e] << 16),
+                                            __uint_as_float(hv[cc][e] & 0xFFFF0000u));
                     const float2 lo = upk2(sub2(pk2(v.x, v.y), h2));
-                    lv[e] = pack_bf16(lo.x, lo.y);
+                    lv[cc][e] = pack_bf16(lo.x, lo.y);
                 }
             }
         }
-        store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv, lv, g0, g1);
     }
+    wait();
+#pragma unroll
+    for (int cc = 0; cc < NG; ++cc)
+        store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv[cc], lv[cc], g0, g1);
 }
 
 }  // namespace
