@@ -18,6 +18,7 @@ on the same inputs; e2e times srp_map_host with pinned host buffers.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -759,13 +760,24 @@ def serve_run(srp, plans, cfgs, rate, duration, seed):
             rid = srv.submit(s, cfgs[s]["Y"][b * SERVE_BLOCK:(b + 1) * SERVE_BLOCK], tag=k)
             lag[rid] = time.perf_counter() - t0 - sched[k]
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    done = []
-    while th.is_alive():
-        done += srv.poll(wait_ms=20)
-    th.join()
-    done += srv.drain(timeout_s=120.0)
+    # the load generator must not be held up by the collector: no garbage
+    # collection pauses and short GIL hand-overs while requests arrive
+    switch = sys.getswitchinterval()
+    gc_on = gc.isenabled()
+    gc.disable()
+    sys.setswitchinterval(1e-4)
+    try:
+        th = threading.Thread(target=submitter)
+        th.start()
+        done = []
+        while th.is_alive():
+            done += srv.poll(wait_ms=20)
+        th.join()
+        done += srv.drain(timeout_s=120.0)
+    finally:
+        sys.setswitchinterval(switch)
+        if gc_on:
+            gc.enable()
     t_end = time.perf_counter() - t0
     st = srv.stats
     srv.close()
