@@ -200,7 +200,10 @@ SRP_API srp_status srp_plan_tdoa(srp_handle h, double *x_host);
  *           writing maps (argmax and peak are still produced);
  *   d_argmax device [L] int32: lowest-index maximiser of each frame's map;
  *   d_peak  device [L] float map value at d_argmax, or NULL.
- * Asynchronous on stream s.                                               */
+ * Asynchronous on stream s.  The tensor-core engine runs three kernels
+ * (GCC samples or conventional operands, formed from STFT input directly;
+ * the map contraction; the per-frame argmax), the CUDA-core engine four
+ * (cross spectra first).                                                  */
 SRP_API srp_status srp_map(srp_handle h, const void *d_in, int32_t L, float *d_maps,
                    int32_t *d_argmax, float *d_peak, srp_stream_t s);
 
@@ -277,7 +280,9 @@ SRP_API srp_status srp_poll_device_status(srp_handle h, srp_stream_t s);
 /* Per-stage timing: when enabled, srp_map records CUDA events around each
  * stage on its stream; srp_stage_times waits for the last call's events and
  * returns milliseconds per stage in ms[0..n): 0 cross spectra, 1 GCC
- * samples, 2 map contraction, 3 argmax reduction (0 for a skipped stage). */
+ * samples, 2 map contraction, 3 argmax reduction (0 for a skipped stage;
+ * on the tensor-core engine stage 1 includes forming the cross spectra, and
+ * stage 0 is 0).                                                          */
 SRP_API srp_status srp_set_timing(srp_handle h, int32_t enable);
 SRP_API srp_status srp_stage_times(srp_handle h, float *ms, int32_t n);
 

@@ -405,7 +405,10 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     for (int &r : h->stage_ran) r = 0;
     record(h, 0, s);
     const float2 *psi = static_cast<const float2 *>(d_in);
-    if (h->input_kind == SRP_IN_STFT) {
+    // The tensor-core operand kernels form the weighted cross spectra of STFT
+    // input themselves; the CUDA-core engine runs K1 first.
+    const bool from_y = lay.tc && h->input_kind == SRP_IN_STFT;
+    if (h->input_kind == SRP_IN_STFT && !lay.tc) {
         SRP_CUDA(launch_phat(static_cast<const float2 *>(d_in), L, lay.M, lay.Kb, h->d_pairs,
                              lay.Q, h->weighting, h->d_psi, s), "cross-spectrum kernel");
         psi = h->d_psi;
@@ -415,13 +418,15 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     record(h, 1, s);
     const int fmt = h->precision == SRP_PREC_FP32 ? 1 : (h->precision == SRP_PREC_FP16 ? 2 : 0);
     if (h->mode == SRP_MODE_CONV && lay.tc) {
-        SRP_CUDA(launch_conv_operand_tc(psi, L, lay.Q, lay.K, h->d_offc, h->d_xi16, lay.L_pad,
-                                        lay.Sc, fmt, s), "conventional operand kernel");
+        SRP_CUDA(launch_conv_operand_tc(psi, from_y, lay.M, h->d_pairs, h->weighting, L, lay.Q,
+                                        lay.K, h->d_offc, h->d_xi16, lay.L_pad, lay.Sc, fmt,
+                                        h->d_part, s), "conventional operand kernel");
         h->stage_ran[kStageGcc] = 1;
         ++launches;
     } else if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
-        SRP_CUDA(launch_gcc_samples_tc(psi, L, lay.Q, lay.K, h->d_nq, h->d_offc, lay.n_aux,
-                                       h->d_twid, h->d_xi16, lay.L_pad, lay.Sc, fmt, s),
+        SRP_CUDA(launch_gcc_samples_tc(psi, from_y, lay.M, h->d_pairs, h->weighting, L, lay.Q,
+                                       lay.K, h->d_nq, h->d_offc, lay.n_aux, h->d_twid,
+                                       h->d_xi16, lay.L_pad, lay.Sc, fmt, h->d_part, s),
                  "GCC sample kernel");
         h->stage_ran[kStageGcc] = 1;
         ++launches;
@@ -450,7 +455,10 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     h->stage_ran[kStageMap] = 1;
     ++launches;
     record(h, 3, s);
-    SRP_CUDA(launch_argmax(h->d_part, lay.n_tiles, L, d_argmax, d_peak, s), "argmax kernel");
+    // tensor-core tiles raise one key per frame (d_part[0, L)); CUDA-core tiles
+    // leave one key per (frame, tile)
+    SRP_CUDA(launch_argmax(h->d_part, lay.tc ? 1 : lay.n_tiles, L, d_argmax, d_peak, s),
+             "argmax kernel");
     h->stage_ran[kStageArgmax] = 1;
     ++launches;
     record(h, 4, s);

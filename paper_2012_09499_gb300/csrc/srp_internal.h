@@ -148,9 +148,14 @@ cudaError_t launch_conv_simt(const int32_t *x, int64_t J_pad, int64_t J, int Q, 
                              const float2 *psi, int L, float *maps, unsigned long long *part,
                              int n_tiles, cudaStream_t s);
 cudaError_t encode_xi_map(void *xi16, int rows, int S_pad, int N, void *map_out);
-cudaError_t launch_gcc_samples_tc(const float2 *psi, int L, int Q, int K, const int32_t *nq,
+// Tensor-core operand kernels: src is the cross spectra psi[L][Q][Kb], or with
+// from_y the STFT frames y[L][M][Kb] (the weighted cross spectra are formed
+// in the kernel).  best (nullable): the L per-frame argmax keys, cleared here.
+cudaError_t launch_gcc_samples_tc(const float2 *src, bool from_y, int M, const int2 *pairs,
+                                  int weighting, int L, int Q, int K, const int32_t *nq,
                                   const int32_t *offc, int n_aux, const float2 *twid,
-                                  uint16_t *xi16, int L_pad, int S_pad, int fmt, cudaStream_t s);
+                                  uint16_t *xi16, int L_pad, int S_pad, int fmt,
+                                  unsigned long long *best, cudaStream_t s);
 int interp_tc_frames_per_cta(int L);
 cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const int4 *ctab,
                              int par1_used, int64_t J_pad, int64_t J, int Q, const int32_t *nq,
@@ -162,8 +167,10 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
 cudaError_t launch_build_w(const int2 *xs, const int4 *ctab, const int32_t *woff, int n_chunks,
                            int64_t J_pad, int xf, int tile_steps, int n_tiles, int precision,
                            void *w, cudaStream_t s);
-cudaError_t launch_conv_operand_tc(const float2 *psi, int L, int Q, int K, const int32_t *offc,
-                                   uint16_t *b16, int L_pad, int S_pad, int fmt, cudaStream_t s);
+cudaError_t launch_conv_operand_tc(const float2 *src, bool from_y, int M, const int2 *pairs,
+                                   int weighting, int L, int Q, int K, const int32_t *offc,
+                                   uint16_t *b16, int L_pad, int S_pad, int fmt,
+                                   unsigned long long *best, cudaStream_t s);
 cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,
                           float *peak, cudaStream_t s);
 

@@ -6,8 +6,9 @@
 //   k_interp_tc       map[l][i] = sum_q sum_n xi_q(n) sinc(x_iq - n)
 //                     (Eq. SRPapprox summed over pairs, Eq. SRP_T_IFT) as one
 //                     (J x S) x (S x L) contraction with the pair sum as the
-//                     reduction axis, accumulated in TMEM, with the maps and
-//                     the per-tile argmax keys written by the epilogue.
+//                     reduction axis, accumulated in TMEM; the epilogue
+//                     writes the maps and raises each frame's argmax key
+//                     (atomicMax over the candidate tiles).
 //
 // Operand A (sinc weights) is generated on chip.  With x = x0 + f,
 //   sinc(x - n) = (-1)^n * [(-1)^x0 sin(pi f) / pi] / (f + x0 - n),
@@ -53,17 +54,40 @@ using namespace tc;
 
 // ---------------------------------------------------------------------------
 // GCC samples as 16-bit operand B: xi'[row][slot], row = frame (hi) or
-// L_pad + frame (lo), slot = offc[q] + t, value (-1)^n xi_q(n).
+// L_pad + frame (lo), slot = offc[q] + t, value (-1)^n xi_q(n).  With kFromY
+// the row's cross spectrum is formed here from the STFT frames (the weighted
+// y_m conj(y_m') of K1, the same arithmetic), so K1 and its round trip
+// through the cross-spectrum scratch are skipped.  CTA (0, 0) also clears
+// the per-frame argmax keys that the map kernel's tiles raise with atomicMax.
 // ---------------------------------------------------------------------------
-template <int kFmt>  // 0: bf16, 1: bf16 hi/lo split, 2: fp16
+template <int kFmt, bool kFromY>  // kFmt 0: bf16, 1: bf16 hi/lo split, 2: fp16
 __global__ void __launch_bounds__(128) k_gcc_samples_tc(
-    const float2 *__restrict__ psi, int Q, int K, const int32_t *__restrict__ nq,
-    const int32_t *__restrict__ offc, int n_aux, const float2 *__restrict__ twid,
-    uint16_t *__restrict__ xi16, int L_pad, int S_pad) {
+    const float2 *__restrict__ src, int M, const int2 *__restrict__ pairs, int weighting, int Q,
+    int K, const int32_t *__restrict__ nq, const int32_t *__restrict__ offc, int n_aux,
+    const float2 *__restrict__ twid, uint16_t *__restrict__ xi16, int L_pad, int S_pad,
+    unsigned long long *__restrict__ best) {
     extern __shared__ float2 sm[];
     float2 *tw = sm, *ps = sm + K;
-    const int q = blockIdx.x, l = blockIdx.y;
-    stage_gcc_row(psi + ((size_t)l * Q + q) * (K / 2 + 1), twid, K, tw, ps);
+    const int q = blockIdx.x, l = blockIdx.y, Kb = K / 2 + 1;
+    if (best != nullptr && q == 0 && l == 0)
+        for (int i = threadIdx.x; i < (int)gridDim.y; i += blockDim.x) best[i] = 0ull;
+    if (kFromY) {
+        const int2 p = pairs[q];
+        const float2 *ym = src + ((size_t)l * M + p.x) * Kb, *yn = src + ((size_t)l * M + p.y) * Kb;
+        for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = twid[j];
+        for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
+            float2 a = ym[k], b = yn[k];
+            if (weighting == SRP_WEIGHT_PHAT) {
+                a = unit_phase(a);
+                b = unit_phase(b);
+            }
+            const float2 v = times_conj(a, b);
+            const float w = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
+            ps[k] = make_float2(w * v.x, w * v.y);
+        }
+    } else {
+        stage_gcc_row(src + ((size_t)l * Q + q) * Kb, twid, K, tw, ps);
+    }
     __syncthreads();
     const int base = offc[q];
     gcc_row(tw, ps, K, nq[q] + n_aux, [&](int t, int n, float v) {
@@ -87,15 +111,28 @@ __global__ void __launch_bounds__(128) k_gcc_samples_tc(
 // Conventional operand B: slot offc[q] + 2k (+1) of row l holds
 // (a_k/K) Re psi_q(k) (and (a_k/K) Im psi_q(k)), as bf16 (hi, lo) or fp16.
 // ---------------------------------------------------------------------------
-template <int kFmt>  // 0: bf16, 1: bf16 hi/lo split, 2: fp16
-__global__ void __launch_bounds__(128) k_conv_operand_tc(const float2 *__restrict__ psi, int Q,
-                                                         int K, const int32_t *__restrict__ offc,
-                                                         uint16_t *__restrict__ b16, int L_pad,
-                                                         int S_pad) {
+template <int kFmt, bool kFromY>  // kFmt 0: bf16, 1: bf16 hi/lo split, 2: fp16
+__global__ void __launch_bounds__(128) k_conv_operand_tc(
+    const float2 *__restrict__ src, int M, const int2 *__restrict__ pairs, int weighting, int Q,
+    int K, const int32_t *__restrict__ offc, uint16_t *__restrict__ b16, int L_pad, int S_pad,
+    unsigned long long *__restrict__ best) {
     const int Kb = K / 2 + 1;
     const int k = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y, l = blockIdx.z;
+    if (best != nullptr && blockIdx.x == 0 && q == 0 && l == 0)
+        for (int i = threadIdx.x; i < (int)gridDim.z; i += blockDim.x) best[i] = 0ull;
     if (k >= Kb) return;
-    const float2 v = psi[((size_t)l * Q + q) * Kb + k];
+    float2 v;
+    if (kFromY) {  // the weighted cross spectrum of K1, formed here
+        const int2 p = pairs[q];
+        float2 a = src[((size_t)l * M + p.x) * Kb + k], b = src[((size_t)l * M + p.y) * Kb + k];
+        if (weighting == SRP_WEIGHT_PHAT) {
+            a = unit_phase(a);
+            b = unit_phase(b);
+        }
+        v = times_conj(a, b);
+    } else {
+        v = src[((size_t)l * Q + q) * Kb + k];
+    }
     const float ak = ((k == 0 || 2 * k == K) ? 1.0f : 2.0f) / (float)K;
     const float re = ak * v.x, im = ak * v.y;
     const size_t hi = (size_t)l * S_pad + offc[q] + 2 * k;
@@ -420,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             }
             const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, 1);
             key = other > key ? other : key;
-            if (h == 0 && fr < n_rows) a.part[(size_t)(l0 + fr) * a.n_tiles + blockIdx.x] = key;
+            if (h == 0 && fr < n_rows && key != 0ull) atomicMax(a.part + l0 + fr, key);
         }
     } else if (warp == kTmaWarp) {
         // ---------------- B loads (GCC samples) ----------------
@@ -596,31 +633,46 @@ cudaError_t encode_xi_map(void *xi16, int rows, int S_pad, int N, void *map_out)
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_gcc_samples_tc(const float2 *psi, int L, int Q, int K, const int32_t *nq,
+cudaError_t launch_gcc_samples_tc(const float2 *src, bool from_y, int M, const int2 *pairs,
+                                  int weighting, int L, int Q, int K, const int32_t *nq,
                                   const int32_t *offc, int n_aux, const float2 *twid,
-                                  uint16_t *xi16, int L_pad, int S_pad, int fmt, cudaStream_t s) {
+                                  uint16_t *xi16, int L_pad, int S_pad, int fmt,
+                                  unsigned long long *best, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * (size_t)(K + K / 2 + 1);
-    static bool attr[3] = {false, false, false};
-    auto kern = fmt == 0 ? k_gcc_samples_tc<0> : (fmt == 1 ? k_gcc_samples_tc<1> : k_gcc_samples_tc<2>);
-    if (!attr[fmt]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    typedef void (*Kern)(const float2 *, int, const int2 *, int, int, int, const int32_t *,
+                         const int32_t *, int, const float2 *, uint16_t *, int, int,
+                         unsigned long long *);
+    static const Kern kerns[6] = {k_gcc_samples_tc<0, false>, k_gcc_samples_tc<1, false>,
+                                  k_gcc_samples_tc<2, false>, k_gcc_samples_tc<0, true>,
+                                  k_gcc_samples_tc<1, true>,  k_gcc_samples_tc<2, true>};
+    static bool attr[6] = {false, false, false, false, false, false};
+    const int v = fmt + (from_y ? 3 : 0);
+    if (!attr[v]) {
+        cudaError_t e = cudaFuncSetAttribute(kerns[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(sizeof(float2) * (8192 + 4097)));
         if (e != cudaSuccess) return e;
-        attr[fmt] = true;
+        attr[v] = true;
     }
-    kern<<<dim3(Q, L), 128, smem, s>>>(psi, Q, K, nq, offc, n_aux, twid, xi16, L_pad, S_pad);
+    kerns[v]<<<dim3(Q, L), 128, smem, s>>>(src, M, pairs, weighting, Q, K, nq, offc, n_aux, twid,
+                                           xi16, L_pad, S_pad, best);
     return cudaGetLastError();
 }
 
-cudaError_t launch_conv_operand_tc(const float2 *psi, int L, int Q, int K, const int32_t *offc,
-                                   uint16_t *b16, int L_pad, int S_pad, int fmt, cudaStream_t s) {
+cudaError_t launch_conv_operand_tc(const float2 *src, bool from_y, int M, const int2 *pairs,
+                                   int weighting, int L, int Q, int K, const int32_t *offc,
+                                   uint16_t *b16, int L_pad, int S_pad, int fmt,
+                                   unsigned long long *best, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
     const int Kb = K / 2 + 1;
     dim3 grid((Kb + 127) / 128, Q, L);
-    if (fmt == 0) k_conv_operand_tc<0><<<grid, 128, 0, s>>>(psi, Q, K, offc, b16, L_pad, S_pad);
-    else if (fmt == 1) k_conv_operand_tc<1><<<grid, 128, 0, s>>>(psi, Q, K, offc, b16, L_pad, S_pad);
-    else k_conv_operand_tc<2><<<grid, 128, 0, s>>>(psi, Q, K, offc, b16, L_pad, S_pad);
+    typedef void (*Kern)(const float2 *, int, const int2 *, int, int, int, const int32_t *,
+                         uint16_t *, int, int, unsigned long long *);
+    static const Kern kerns[6] = {k_conv_operand_tc<0, false>, k_conv_operand_tc<1, false>,
+                                  k_conv_operand_tc<2, false>, k_conv_operand_tc<0, true>,
+                                  k_conv_operand_tc<1, true>,  k_conv_operand_tc<2, true>};
+    kerns[fmt + (from_y ? 3 : 0)]<<<grid, 128, 0, s>>>(src, M, pairs, weighting, Q, K, offc, b16,
+                                                       L_pad, S_pad, best);
     return cudaGetLastError();
 }
 
