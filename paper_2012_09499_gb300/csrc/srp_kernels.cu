@@ -234,6 +234,9 @@ __global__ void __launch_bounds__(256) k_argmax(const unsigned long long *__rest
     __shared__ unsigned long long red[8];
     const int l = blockIdx.x;
     unsigned long long k = 0ull;
+    // launched behind the map kernel with programmatic stream serialization:
+    // wait until that kernel's keys are complete and visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
         const unsigned long long v = part[(size_t)l * n_tiles + t];
         k = v > k ? v : k;
@@ -305,7 +308,17 @@ cudaError_t launch_conv_simt(const int32_t *x, int64_t J_pad, int64_t J, int Q, 
 cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,
                           float *peak, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
-    k_argmax<<<L, 256, 0, s>>>(part, n_tiles, argmax, peak);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)L);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_argmax, part, n_tiles, argmax, peak);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

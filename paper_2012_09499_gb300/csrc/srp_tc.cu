@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(128) k_gcc_samples_tc(
     extern __shared__ float2 sm[];
     float2 *tw = sm, *ps = sm + K;
     const int q = blockIdx.x, l = blockIdx.y, Kb = K / 2 + 1;
+    grid_dep_launch();  // the map kernel may start its prologue now
     if (best != nullptr && q == 0 && l == 0)
         for (int i = threadIdx.x; i < (int)gridDim.y; i += blockDim.x) best[i] = 0ull;
     if (kFromY) {
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(128) k_conv_operand_tc(
     unsigned long long *__restrict__ best) {
     const int Kb = K / 2 + 1;
     const int k = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y, l = blockIdx.z;
+    grid_dep_launch();  // the map kernel may start its prologue now
     if (best != nullptr && blockIdx.x == 0 && q == 0 && l == 0)
         for (int i = threadIdx.x; i < (int)gridDim.z; i += blockDim.x) best[i] = 0ull;
     if (k >= Kb) return;
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
         fence_barrier_init();
     }
     if (warp == kTmaWarp) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    grid_dep_launch();  // the argmax kernel may be scheduled behind this grid
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -397,6 +400,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
 
         // ---------------- epilogue: TMEM -> smem tile -> maps + argmax keys ----------------
         mbar_wait(accum_bar, 0, abort_flag, a.status);
+        grid_dep_wait();  // the operand kernel cleared the frames' keys
         tc_fence_after();
         fence_proxy_async();
         // every MMA has completed (and with it every TMA load it consumed), so the
@@ -464,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
         if (lane == 0) {
             const uint32_t bytes = (kSplit ? 2u : 1u) * b_tile;
             int issued = 0;
+            grid_dep_wait();  // operand B is written by the previous kernel
             for (int c = 0; c < a.n_chunks; ++c) {
                 const int st = c % a.stages;
                 const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
@@ -605,8 +610,20 @@ cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_interp_tc<kSplit, kHalf, kConv, kTm, kW>
-        <<<dim3((unsigned)a.n_tiles, grid_y), kThreads, smem, s>>>(map, a);
+    // programmatic stream serialization: the prologue (TMEM allocation, barrier
+    // set-up, the first TDOA loads) overlaps the end of the operand kernel
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)a.n_tiles, grid_y);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_interp_tc<kSplit, kHalf, kConv, kTm, kW>, map, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
