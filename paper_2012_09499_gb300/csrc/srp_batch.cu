@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128) k_batch_operands(const BatchInst *__restr
     // Nyquist: a_k psi of every pair of the block, then its critical samples.
     // The loads of a bin for all the block's pairs are issued before any
     // arithmetic, so that their latencies overlap.
-    for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = I.twid[j];
+    copy_twiddles_async(I.twid, K, tw);
     const bool stft = I.input_kind == SRP_IN_STFT;
     for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
         float2 u[kPairBlock], v[kPairBlock];
@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(128) k_batch_operands(const BatchInst *__restr
             }
         }
     }
+    wait_async_copies();
     __syncthreads();
     gcc_rows(tw, ps, Kb, np, K, [&](int j) { return I.nq[q0 + j] + I.n_aux; },
              [&](int j, int t, int nl, float v) {

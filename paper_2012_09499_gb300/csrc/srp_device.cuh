@@ -157,17 +157,50 @@ __device__ __forceinline__ float2 times_conj(float2 a, float2 b) {
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// Stage one (frame, pair) spectrum row as a_k psi(k) and the twiddles.
+// Start copying the K twiddles into shared memory tw (16-byte cp.async, two
+// per copy; K even, both addresses 16-byte aligned).  The copies complete at
+// wait_async_copies().
+__device__ __forceinline__ void copy_twiddles_async(const float2 *__restrict__ twid, int K,
+                                                    float2 *tw) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(tw);
+    for (int j = 2 * (int)threadIdx.x; j < K; j += 2 * (int)blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 8u * (uint32_t)j),
+                     "l"(twid + j)
+                     : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void wait_async_copies() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Bins of a spectrum row handled together by a thread: their loads are issued
+// before any arithmetic, so that the latencies overlap.
+constexpr int kStageUnroll = 4;
+
+// Stage one (frame, pair) spectrum row as a_k psi(k) and the twiddles
+// (the caller synchronises the block before use).
 __device__ __forceinline__ void stage_gcc_row(const float2 *__restrict__ row,
                                               const float2 *__restrict__ twid, int K, float2 *tw,
                                               float2 *ps) {
     const int Kb = K / 2 + 1;
-    for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = twid[j];
-    for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
-        const float2 v = row[k];
-        const float a = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
-        ps[k] = make_float2(a * v.x, a * v.y);
+    copy_twiddles_async(twid, K, tw);
+    const int nt = blockDim.x;
+    for (int k0 = threadIdx.x; k0 < Kb; k0 += kStageUnroll * nt) {
+        float2 v[kStageUnroll];
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u)
+            if (k0 + u * nt < Kb) v[u] = row[k0 + u * nt];
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const int k = k0 + u * nt;
+            if (k < Kb) {
+                const float a = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
+                ps[k] = make_float2(a * v[u].x, a * v[u].y);
+            }
+        }
     }
+    wait_async_copies();
 }
 
 }  // namespace dev

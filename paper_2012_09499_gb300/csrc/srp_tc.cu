@@ -75,17 +75,31 @@ __global__ void __launch_bounds__(128) k_gcc_samples_tc(
     if (kFromY) {
         const int2 p = pairs[q];
         const float2 *ym = src + ((size_t)l * M + p.x) * Kb, *yn = src + ((size_t)l * M + p.y) * Kb;
-        for (int j = threadIdx.x; j < K; j += blockDim.x) tw[j] = twid[j];
-        for (int k = threadIdx.x; k < Kb; k += blockDim.x) {
-            float2 a = ym[k], b = yn[k];
-            if (weighting == SRP_WEIGHT_PHAT) {
-                a = unit_phase(a);
-                b = unit_phase(b);
+        copy_twiddles_async(twid, K, tw);
+        const int nt = blockDim.x;
+        for (int k0 = threadIdx.x; k0 < Kb; k0 += kStageUnroll * nt) {
+            float2 a[kStageUnroll], b[kStageUnroll];
+#pragma unroll
+            for (int u = 0; u < kStageUnroll; ++u)
+                if (k0 + u * nt < Kb) {
+                    a[u] = ym[k0 + u * nt];
+                    b[u] = yn[k0 + u * nt];
+                }
+#pragma unroll
+            for (int u = 0; u < kStageUnroll; ++u) {
+                const int k = k0 + u * nt;
+                if (k >= Kb) continue;
+                float2 x = a[u], y = b[u];
+                if (weighting == SRP_WEIGHT_PHAT) {
+                    x = unit_phase(x);
+                    y = unit_phase(y);
+                }
+                const float2 v = times_conj(x, y);
+                const float w = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
+                ps[k] = make_float2(w * v.x, w * v.y);
             }
-            const float2 v = times_conj(a, b);
-            const float w = (k == 0 || 2 * k == K) ? 1.0f : 2.0f;
-            ps[k] = make_float2(w * v.x, w * v.y);
         }
+        wait_async_copies();
     } else {
         stage_gcc_row(src + ((size_t)l * Q + q) * Kb, twid, K, tw, ps);
     }
