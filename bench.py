@@ -37,8 +37,8 @@ UNIT = "cells*pairs/s"
 WORKLOAD = dict(name="room_3d", M=8, J=480000, K=1024, L=64, n_aux=2, fs=16000.0, snr_db=10.0)
 FLUSH_BYTES = 256 << 20
 # DRAM read + write bytes of one k_interp_tc<split> launch on this workload,
-# from ncu (profiles/launches_room_3d.md); None once the kernel changes.
-K3_TRAFFIC_BYTES = 184.4e6
+# from ncu (profiles/k_interp_tc_room_3d.md); None once the kernel changes.
+K3_TRAFFIC_BYTES = 185.1e6
 
 
 def config_dict(Q, S):
@@ -241,12 +241,10 @@ def bench_ours(args):
     for mode in ("nyquist", "conventional"):
         plans[mode] = srp.Plan(mic, grid, w["fs"], 343.0, w["K"], mode=mode, n_aux=w["n_aux"],
                                max_frames=L, host_io=2 if mode == "nyquist" else 0)
-        srp.srp_set_timing(plans[mode].handle, True)
     # the conventional map on the CUDA cores too (the plain GPU path)
     plans["conventional_cuda_cores"] = srp.Plan(mic, grid, w["fs"], 343.0, w["K"],
                                                 mode="conventional", max_frames=L,
                                                 engine="cuda_cores")
-    srp.srp_set_timing(plans["conventional_cuda_cores"].handle, True)
     ny = plans["nyquist"]
     Q, S = ny.info.Q, ny.info.S
 
@@ -255,8 +253,20 @@ def bench_ours(args):
             srp.srp_map(plan.handle, d_in[k % len(d_in)], L, maps, am, pk, stream)
         return step
 
-    def stage_time(plan):
-        return lambda: srp.srp_stage_times(plan.handle)["map"]
+    def stage_runs(plan, n=5):
+        """Per-stage times from the library's own events, on n separate steps
+        (L2 flushed before each).  The timed steps run with these events off:
+        events between the kernels would serialise their programmatic
+        launches."""
+        srp.srp_set_timing(plan.handle, True)
+        runs = []
+        for k in range(n):
+            flush(k)
+            make_step(plan)(k)
+            runs.append(srp.srp_stage_times(plan.handle))
+        srp.srp_set_timing(plan.handle, False)
+        return (np.array([r["map"] for r in runs]),
+                {key: float(np.mean([r[key] for r in runs])) for key in runs[0]})
 
     res = {}
     with ClockSampler(local) as clk:
@@ -264,11 +274,12 @@ def bench_ours(args):
             steps = args.steps if mode == "nyquist" else max(3, min(args.steps, args.conv_steps))
             if mode == "conventional_cuda_cores":
                 steps = 3
-            ms, st, wall = time_steps(make_step(plan), steps, args.warmup, flush, stream, world,
-                                      stage_time(plan), name=f"room_3d_{mode}")
+            ms, _, wall = time_steps(make_step(plan), steps, args.warmup, flush, stream, world,
+                                     name=f"room_3d_{mode}")
             launches = srp.srp_last_launch_count(plan.handle) * steps
+            st, stages = stage_runs(plan, 5 if mode != "conventional_cuda_cores" else 2)
             res[mode] = dict(ms=ms, stage=st, wall=wall, steps=steps, launches=launches,
-                             stages=srp.srp_stage_times(plan.handle))
+                             stages=stages)
     clocks = clk.summary()
 
     # map error of the Nyquist approximation w.r.t. conventional on one batch
@@ -341,10 +352,10 @@ def bench_ours(args):
     for prec, resident in (("bf16", False), ("fp16", False), ("bf16", True)):
         pl = srp.Plan(mic, grid, w["fs"], 343.0, w["K"], mode="nyquist", n_aux=w["n_aux"],
                       max_frames=L, precision=prec, resident_weights=resident)
-        srp.srp_set_timing(pl.handle, True)
         name = prec + ("_resident_weights" if resident else "")
-        ms_v, st_v, _ = time_steps(make_step(pl), max(3, min(args.steps, 20)), args.warmup,
-                                   flush, stream, world, stage_time(pl), name=f"room_3d_{name}")
+        ms_v, _, _ = time_steps(make_step(pl), max(3, min(args.steps, 20)), args.warmup,
+                                flush, stream, world, name=f"room_3d_{name}")
+        st_v, _ = stage_runs(pl)
         variants[name] = {"ms_per_step": float(ms_v.mean()),
                           "value": world * J * Q * L / (float(ms_v.mean()) * 1e-3),
                           "map_ms": float(st_v.mean()),
@@ -357,7 +368,7 @@ def bench_ours(args):
         pl.close()
 
     conv_tc = bool(plans["conventional"].info.tensor_cores)
-    conv_stages = srp.srp_stage_times(plans["conventional"].handle)
+    conv_stages = res["conventional"]["stages"]
     for pl in plans.values():
         pl.close()
     extra = {}
