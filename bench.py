@@ -37,8 +37,8 @@ UNIT = "cells*pairs/s"
 WORKLOAD = dict(name="room_3d", M=8, J=480000, K=1024, L=64, n_aux=2, fs=16000.0, snr_db=10.0)
 FLUSH_BYTES = 256 << 20
 # DRAM read + write bytes of one k_interp_tc<split> launch on this workload,
-# from ncu (profiles/k_interp_tc_room_3d.md); None once the kernel changes.
-K3_TRAFFIC_BYTES = 185.1e6
+# from ncu (profiles/launches_room_3d.md); None once the kernel changes.
+K3_TRAFFIC_BYTES = 182.9e6
 
 
 def config_dict(Q, S):
