@@ -397,7 +397,9 @@ void record(srp_plan_s *h, int idx, cudaStream_t s) {
     if (h->timing) cudaEventRecord(h->ev[idx], s);
 }
 
-// The hot path: K1 (STFT input) -> K2 + K3 (Nyquist) or K4 (conventional) -> K5.
+// The hot path: K2 + K3 (Nyquist) or K4 (conventional) -> K5; the CUDA-core
+// engine runs K1 first on STFT input, the tensor-core operand kernels form the
+// cross spectra themselves.
 srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_t *d_argmax,
                    float *d_peak, cudaStream_t s) {
     const Layout &lay = h->lay;

@@ -83,7 +83,9 @@ struct srp_plan_s {
     int4 *d_ctab = nullptr;        // [n_chunks] (pair, bits of nmax - first slot, groups, MMA steps)
     int *d_status = nullptr;       // device error flags (bit 0: a bounded wait gave up)
     alignas(64) unsigned char xi_map[128] = {};  // CUtensorMap of d_xi16
-    unsigned long long *d_part = nullptr;  // [L_pad][n_tiles] per-tile argmax keys
+    // argmax keys, [L_pad][n_tiles]: one per (frame, tile) on the CUDA-core
+    // engine; the tensor-core engine uses the first L, one per frame
+    unsigned long long *d_part = nullptr;
     // staging for srp_map_host (slot 0) and srp_map_host_async (slots 0, 1)
     // (owned, optional): n_slots consecutive slots per buffer
     int n_slots = 0;
