@@ -36,9 +36,37 @@ METRIC = "SRP cells*pairs/s (Nyquist vs conventional) at stated map error; p50/p
 UNIT = "cells*pairs/s"
 WORKLOAD = dict(name="room_3d", M=8, J=480000, K=1024, L=64, n_aux=2, fs=16000.0, snr_db=10.0)
 FLUSH_BYTES = 256 << 20
-# DRAM read + write bytes of one k_interp_tc<split> launch on this workload,
-# from ncu (profiles/launches_room_3d.md); None once the kernel changes.
-K3_TRAFFIC_BYTES = 182.9e6
+# The kernel sources whose DRAM traffic a recorded ncu capture describes.
+KERNEL_SOURCES = ("srp_tc.cu", "srp_tc_common.cuh", "srp_device.cuh", "srp_batch.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def kernel_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 over the kernel sources listed in
+    KERNEL_SOURCES (in that order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2012_09499_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key: str):
+    """DRAM bytes (read + write) per launch of kernel `key` from one ncu
+    capture, as recorded in the profiles' traffic table ("key hash bytes"
+    per line), or None when there is no record for the current kernel
+    sources (the counters describe an older build)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    h = kernel_source_hash()
+    for r in rows:
+        if len(r) >= 3 and r[0] == key and r[1] == h:
+            return float(r[2])
+    return None
 
 
 def config_dict(Q, S):
@@ -344,8 +372,11 @@ def bench_ours(args):
     flops = 2.0 * J * S * L  # multiply-adds of the interpolation contraction, C_int x L
     achieved = flops / (k3_ms * 1e-3) / 1e12
     bf16_peak, peak_src = measured_bf16_peak()
-    # FP32 accuracy is three BF16 products per multiply-add, so its peak is a third
-    split_peak = bf16_peak / 3.0
+    hbm_peak, hbm_src = measured_hbm_peak()
+    # the GCC-sample stage (with the PHAT cross spectra): STFT frames in,
+    # 16-bit operand B out (hi and lo parts for the FP32 split)
+    k2_ms = float(res["nyquist"]["stages"]["gcc_samples"])
+    k2_bytes = 8.0 * L * w["M"] * (w["K"] // 2 + 1) + 2.0 * 2.0 * L * S
 
     # reduced-precision variants of the same step (Nyquist, tensor cores)
     variants = {}
@@ -410,13 +441,27 @@ def bench_ours(args):
         "stage_ms_conventional": conv_stages,
         "roofline": {
             "kernel": "k_interp_tc<split> (on-chip sinc weights + tcgen05 MMA, FP32 as 3 BF16 products)",
-            "bound": "tensor", "achieved": achieved, "peak": split_peak, "unit": "TFLOP/s",
-            "frac": achieved / split_peak,
-            "traffic": K3_TRAFFIC_BYTES,
-            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
+            "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": achieved / bf16_peak,
+            "traffic": recorded_traffic("k_interp_tc_fp32_room_3d"),
+            "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
+                             "the current kernel sources (null if none was captured)"),
             "algorithmic": f"2*J*S*L = {flops:.4g} flop per launch (S={S} lags); "
                            f"{k3_ms:.4f} ms per launch",
-            "peak_source": f"measured bf16 {bf16_peak:.1f} TFLOP/s ({peak_src}) / 3 products",
+            "peak_source": f"measured bf16 burst {bf16_peak:.1f} TFLOP/s ({peak_src})",
+            "tensor_products_per_mac": 3,
+            "tensor_pipe_frac": 3.0 * achieved / bf16_peak,
+            "tensor_pipe_note": ("FP32 accuracy takes three BF16 products per multiply-add; "
+                                 "tensor_pipe_frac counts them, frac counts the method's flops"),
+        },
+        "roofline_gcc_samples": {
+            "kernel": "k_gcc_samples_tc<split, from STFT> (PHAT cross spectra + critical GCC samples)",
+            "bound": "hbm", "achieved": k2_bytes / (k2_ms * 1e-3) / 1e9, "peak": hbm_peak,
+            "unit": "GB/s", "frac": k2_bytes / (k2_ms * 1e-3) / 1e9 / hbm_peak,
+            "traffic": recorded_traffic("k_gcc_samples_tc_fp32_room_3d"),
+            "algorithmic": (f"8*L*M*Kb STFT in + 2*2*L*S operand B out = {k2_bytes:.4g} B per "
+                            f"launch; {k2_ms:.4f} ms per launch"),
+            "peak_source": f"measured HBM copy {hbm_peak:.0f} GB/s ({hbm_src})",
         },
         "precision_variants": variants,
         "e2e": {"value": world * cells / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
@@ -437,6 +482,13 @@ def bench_ours(args):
         "cpu_baseline": cpu,
     }
     line.update(extra)
+    if "serving" in extra:  # a compact copy of the serving loop's headline figures
+        line["serving_summary"] = {
+            k: {"maps_per_s": v["maps_per_s"], "offered_frames_per_s": v["offered_frames_per_s"],
+                "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"],
+                "tensor_core_streams": v["tensor_core_streams"],
+                "overlapped_iterations_frac": v["overlapped_iterations_frac"]}
+            for k, v in extra["serving"].items() if isinstance(v, dict) and "p99_ms" in v}
     print(json.dumps(line))
 
 
@@ -486,6 +538,9 @@ def bench_batched(args, flush, stream):
                  for c in cfgs]
         S = np.array([p.info.S for p in plans], np.float64)
         flops = float((2.0 * Js * S * BATCH_L).sum())
+        Kbs = np.array([c["K"] // 2 + 1 for c in cfgs], np.float64)
+        op_bytes = float((8.0 * BATCH_L * Ms * Kbs).sum() +
+                         (2.0 * (2.0 if prec == "fp32" else 1.0) * BATCH_L * S).sum())
         batch = srp.Batch(plans)
         outs = batch.outputs(L, "cuda")
         maps, ams, pks = [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs]
@@ -507,7 +562,7 @@ def bench_batched(args, flush, stream):
         srp.srp_batch_poll_device_status(batch.handle)
         stage = {key: float(np.mean([x[key] for x in st])) for key in st[0]}
         info = batch.info
-        peak = bf16_peak / 3.0 if prec == "fp32" else bf16_peak
+        peak = bf16_peak
         achieved = flops / (stage["map"] * 1e-3) / 1e12
         wbytes = float(sum(p.info.weight_bytes for p in plans))
         out[name] = {
@@ -535,9 +590,16 @@ def bench_batched(args, flush, stream):
                          {"kernel": "k_map_batch_tc (persistent, on-chip sinc weights)",
                           "bound": "tensor", "achieved": achieved, "peak": peak,
                           "unit": "TFLOP/s", "frac": achieved / peak,
+                          "tensor_products_per_mac": 3 if prec == "fp32" else 1,
                           "algorithmic": f"sum 2*J*S*L = {flops:.4g} flop per launch",
-                          "peak_source": f"measured bf16 {bf16_peak:.1f} TFLOP/s ({peak_src})"
-                                         + (" / 3 products" if prec == "fp32" else "")}),
+                          "peak_source": f"measured bf16 burst {bf16_peak:.1f} TFLOP/s "
+                                         f"({peak_src})"}),
+            "roofline_operands": {
+                "kernel": "k_batch_operands (PHAT cross spectra + critical GCC samples)",
+                "bound": "hbm", "unit": "GB/s", "peak": measured_hbm_peak()[0],
+                "achieved": op_bytes / (stage["operands"] * 1e-3) / 1e9,
+                "frac": op_bytes / (stage["operands"] * 1e-3) / 1e9 / measured_hbm_peak()[0],
+                "algorithmic": f"STFT in + operand B out = {op_bytes:.4g} B per launch"},
         }
         batch.close()
         for p in plans:
@@ -805,6 +867,8 @@ def serve_run(srp, plans, cfgs, rate, duration, seed):
     run = np.array([d["t_done"] - d["t_start"] for d in ok])     # its iteration, copies included
     frames = sum(d["L"] for d in ok)
     cp = sum(d["L"] * plans[d["stream"]].info.J * plans[d["stream"]].info.Q for d in ok)
+    per_iter = {d["iteration"]: d["iteration_streams"] for d in ok}
+    n_iter = int(st.iterations - st0.iterations)
     return {"requests": len(done), "completed": len(ok), "frames": frames,
             "maps_per_s": frames / t_end, "cells_pairs_per_s": cp / t_end,
             "offered_frames_per_s": rate, "wall_s": t_end,
@@ -814,7 +878,11 @@ def serve_run(srp, plans, cfgs, rate, duration, seed):
             "queued_p99_ms": float(np.percentile(wait, 99)),
             "iteration_p50_ms": float(np.percentile(run, 50)),
             "iteration_p99_ms": float(np.percentile(run, 99)),
-            "mean_frames_per_iteration": frames / max(1, int(st.iterations - st0.iterations)),
+            "mean_frames_per_iteration": frames / max(1, n_iter),
+            "mean_streams_per_iteration": float(np.mean(list(per_iter.values()))),
+            "max_streams_per_iteration": int(max(per_iter.values())),
+            "overlapped_iterations_frac": (int(st.overlapped_iterations - st0.overlapped_iterations)
+                                           / max(1, n_iter)),
             "kernel_launches": int(st.kernel_launches - st0.kernel_launches),
             "warm_up": f"one {SERVE_BLOCK}-frame block per stream, drained before the schedule",
             "device_bytes_peak": int(st.device_bytes_peak),

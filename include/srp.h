@@ -100,6 +100,12 @@ typedef enum {
     SRP_ENGINE_CUDA_CORES = 1 /* FP32 CUDA-core kernels only (FP32 precision) */
 } srp_engine;
 
+typedef enum {
+    SRP_ARGMAX_RESCORE = 0, /* BF16/FP16 tensor-core plans: the maximiser is chosen in FP32
+                               (see srp_map); FP32 plans: the map's own first maximiser */
+    SRP_ARGMAX_MAP = 1      /* always the first maximiser of the computed map */
+} srp_argmax_mode;
+
 typedef struct {
     int32_t M;                /* microphones, 2 <= M <= 64 */
     const double *mic_xyz;    /* host [M][3] metres; copied by srp_plan */
@@ -128,6 +134,7 @@ typedef struct {
                                  streamed into every map; the rest is generated on chip
                                  while it streams.  0: all generated; 1: all streamed.
                                  The maps are the same either way */
+    srp_argmax_mode argmax;   /* how the per-frame maximiser is decided (default 0) */
 } srp_plan_desc;
 
 /* Sizes of a plan, computed on the host (no device needed). */
@@ -146,6 +153,8 @@ typedef struct {
                              reach half the 1e-4 tolerance */
     size_t device_bytes;  /* bytes srp_plan allocates on the device */
     size_t weight_bytes;  /* of which the resident interpolation matrix (0 if generated) */
+    int32_t argmax_rescored; /* 1: srp_map chooses the maximiser in FP32 (reduced-precision
+                                tensor-core plan with SRP_ARGMAX_RESCORE) */
 } srp_plan_info;
 
 typedef struct srp_plan_s *srp_handle;
@@ -203,7 +212,19 @@ SRP_API srp_status srp_plan_tdoa(srp_handle h, double *x_host);
  * Asynchronous on stream s.  The tensor-core engine runs three kernels
  * (GCC samples or conventional operands, formed from STFT input directly;
  * the map contraction; the per-frame argmax), the CUDA-core engine four
- * (cross spectra first).                                                  */
+ * (cross spectra first).
+ * Reduced precision (BF16/FP16 operands, argmax SRP_ARGMAX_RESCORE): the
+ * maps are those of the reduced-precision contraction, but the maximiser is
+ * decided in FP32.  Let m be the frame's largest map value.  Every
+ * 128-candidate tile whose largest value is at least m - 0.02 |m| (twice the
+ * 1e-2 x peak error bound of these maps below the maximum, so the tile of
+ * the exact maximiser is among them whenever the bound holds and the
+ * frame's peak is its maximum) is evaluated again candidate by candidate in
+ * FP32 (Eq. SRPapprox from FP32 GCC samples, or Eq. GCC_IFT from the FP32
+ * cross spectra), and d_argmax / d_peak are the lowest-index maximiser of
+ * those FP32 values and its FP32 value.  If more than 64 tiles qualify
+ * (a nearly flat map) the frame keeps the first maximiser of its
+ * reduced-precision map.                                                  */
 SRP_API srp_status srp_map(srp_handle h, const void *d_in, int32_t L, float *d_maps,
                    int32_t *d_argmax, float *d_peak, srp_stream_t s);
 
@@ -257,11 +278,12 @@ SRP_API srp_status srp_gcc_samples(srp_handle h, const void *d_in, int32_t L, fl
  *  - twiddles are generated on the device.
  * Inputs: M and K as in srp_plan_desc, n_aux >= 0, Nq host [Q] lag counts
  * (for example from srp_plan_describe, which is host-only), d_y device
- * y[L][M][Kb] complex64.  Output: d_xi device float [L][S], exactly as
- * srp_gcc_samples writes it.  Asynchronous on s.
+ * y[L][M][Kb] complex64, 0 <= L <= 65535.  Output: d_xi device float
+ * [L][S], exactly as srp_gcc_samples writes it.  Asynchronous on s.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and every call
+ * (cudaGetSymbolAddress) and sets the kernels' shared-memory limit, once,
+ * with that device current; make that first call before any stream
+ * capture.  All calls share the one array and every call
  * overwrites the part it reads, so nothing carries over between calls, but
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * on it: order them.                                                     */
@@ -474,13 +496,21 @@ typedef struct {
 
 /* One finished request.  Times are milliseconds since srp_server_create on
  * the host's steady clock: submission, start of its iteration, and the
- * moment its results were in the caller's buffers.                       */
+ * moment its results were in the caller's buffers.  The iteration fields
+ * describe the iteration that mapped it: its sequence number (from 1), how
+ * many streams' groups and frames it carried, and the GPU interval of its
+ * work (CUDA events at the start of its first copy and after its last,
+ * milliseconds since an event recorded at srp_server_create; 0 when the
+ * request did not run).                                                  */
 typedef struct {
     uint64_t request_id, tag;
     int32_t stream, L;
     int32_t status;             /* SRP_OK, SRP_ERR_TIMEOUT (deadline passed before it
                                    started) or the error of its iteration */
+    int32_t iteration_streams, iteration_frames;
+    int64_t iteration;
     double t_submit_ms, t_start_ms, t_done_ms;
+    double t_gpu_start_ms, t_gpu_end_ms;
 } srp_completion;
 
 typedef struct {
@@ -488,6 +518,10 @@ typedef struct {
     int64_t iterations, kernel_launches, admission_waits, queued;
     size_t device_budget_bytes, device_bytes_in_use, device_bytes_peak;
     int32_t batched_streams;    /* streams mapped by the batched launch */
+    int32_t max_iteration_streams;  /* most streams' groups in one iteration */
+    /* iterations whose GPU interval intersected that of another iteration
+     * (their copies and kernels were on the device at the same time)     */
+    int64_t overlapped_iterations;
 } srp_server_stats;
 
 /* Start a server over n plans (stream i maps with plans[i]).  Allocates the
@@ -513,6 +547,14 @@ SRP_API srp_status srp_server_submit(srp_server s, int32_t stream, const void *h
  * count.  wait_ms > 0 waits up to that long for one to finish.            */
 SRP_API srp_status srp_server_poll(srp_server s, srp_completion *out, int32_t max,
                                    int32_t *n_out, int32_t wait_ms);
+
+/* hold != 0: keep queueing submitted requests but start no new iteration
+ * (iterations already on the GPU finish and are delivered); hold = 0:
+ * resume, and the next iterations take everything queued meanwhile (each
+ * stream's group up to its plan's max_frames).  A batching window for a
+ * caller that submits a burst, e.g. frames of many arrays that belong
+ * together.  srp_server_destroy releases a hold.                          */
+SRP_API srp_status srp_server_hold(srp_server s, int32_t hold);
 
 SRP_API srp_status srp_server_get_stats(srp_server s, srp_server_stats *st);
 

@@ -141,6 +141,9 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         lay.n_chunks = (int)(sc / kLagPad);
         lay.N_tc = interp_tc_frames_per_cta(d->max_frames);
     }
+    if (d->argmax != SRP_ARGMAX_RESCORE && d->argmax != SRP_ARGMAX_MAP)
+        return fail(SRP_ERR_INVALID_ARG, "unknown argmax mode");
+    lay.rescore = lay.tc && d->precision != SRP_PREC_FP32 && d->argmax == SRP_ARGMAX_RESCORE;
     if (!(d->resident_fraction >= 0.0f && d->resident_fraction <= 1.0f))
         return fail(SRP_ERR_INVALID_ARG, "resident_fraction must be in [0, 1]");
     if (d->resident_fraction > 0.0f) {
@@ -184,6 +187,11 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
                     ? sizeof(float2) * (size_t)lay.L_max * lay.Q * lay.Kb : 0;
     lay.b_xi = (nyq && !lay.tc) ? sizeof(float) * (size_t)lay.S_pad * lay.L_pad : 0;
     lay.b_xi16 = lay.tc ? sizeof(uint16_t) * (half ? 1 : 2) * (size_t)lay.L_pad * lay.Sc : 0;
+    // FP32 re-scoring: the Nyquist samples in FP32 (the conventional map reads
+    // the cross spectra, formed into b_psi from STFT input)
+    lay.b_xi32 = (lay.rescore && nyq) ? sizeof(float) * (size_t)lay.L_pad * lay.S_pad : 0;
+    lay.b_rs = lay.rescore ? (sizeof(unsigned long long) * (1 + kRescoreCtas) + sizeof(int)) *
+                                 (size_t)lay.L_pad : 0;
     lay.b_offc = lay.tc ? sizeof(int32_t) * lay.Q : 0;
     lay.b_xs = lay.tc ? sizeof(int2) * (size_t)lay.Q * (size_t)lay.J_pad : 0;
     lay.b_ctab = lay.tc ? sizeof(int4) * (size_t)lay.n_chunks : 0;
@@ -229,6 +237,7 @@ void fill_info(const Layout &lay, srp_plan_info *info) {
     info->tensor_cores = lay.tc ? 1 : 0;
     info->device_bytes = lay.total();
     info->weight_bytes = lay.b_w;
+    info->argmax_rescored = lay.rescore ? 1 : 0;
 }
 
 template <typename T>
@@ -247,6 +256,8 @@ void release(srp_plan_s *h) {
     cudaFree(h->d_psi);
     cudaFree(h->d_xi);
     cudaFree(h->d_xi16);
+    cudaFree(h->d_xi32);
+    cudaFree(h->d_rs_fkey);
     cudaFree(h->d_offc);
     cudaFree(h->d_xs);
     cudaFree(h->d_ctab);
@@ -419,16 +430,22 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     }
     record(h, 1, s);
     const int fmt = h->precision == SRP_PREC_FP32 ? 1 : (h->precision == SRP_PREC_FP16 ? 2 : 0);
+    // FP32 re-scoring: per-tile keys instead of one raised key per frame, and
+    // the FP32 operands kept beside the 16-bit ones (cross spectra formed from
+    // STFT input go to d_psi; cross-spectrum input is read in place)
+    unsigned long long *best = lay.rescore ? h->d_rs_fkey : h->d_part;
+    float2 *psi32 = (lay.rescore && from_y) ? h->d_psi : nullptr;
     if (h->mode == SRP_MODE_CONV && lay.tc) {
         SRP_CUDA(launch_conv_operand_tc(psi, from_y, lay.M, h->d_pairs, h->weighting, L, lay.Q,
                                         lay.K, h->d_offc, h->d_xi16, lay.L_pad, lay.Sc, fmt,
-                                        h->d_part, s), "conventional operand kernel");
+                                        best, psi32, s), "conventional operand kernel");
         h->stage_ran[kStageGcc] = 1;
         ++launches;
     } else if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
         SRP_CUDA(launch_gcc_samples_tc(psi, from_y, lay.M, h->d_pairs, h->weighting, L, lay.Q,
                                        lay.K, h->d_nq, h->d_offc, lay.n_aux, h->d_twid,
-                                       h->d_xi16, lay.L_pad, lay.Sc, fmt, h->d_part, s),
+                                       h->d_xi16, lay.L_pad, lay.Sc, fmt, best, h->d_xi32,
+                                       h->d_off, lay.S_pad, s),
                  "GCC sample kernel");
         h->stage_ran[kStageGcc] = 1;
         ++launches;
@@ -444,7 +461,8 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
                                   lay.J_pad, lay.J, lay.Q, h->d_nq, lay.n_aux, lay.xf, lay.Sc,
                                   lay.L_pad, L, h->precision, h->mode == SRP_MODE_CONV ? 1 : 0,
                                   lay.K, d_maps, h->d_part, lay.n_tiles, h->d_status, h->d_w,
-                                  h->d_woff, lay.tile_steps, lay.tile_steps == lay.total_steps, s),
+                                  h->d_woff, lay.tile_steps, lay.tile_steps == lay.total_steps,
+                                  lay.rescore ? h->d_rs_fkey : nullptr, s),
                  "tensor-core map kernel");
     } else if (h->mode == SRP_MODE_NYQUIST) {
         SRP_CUDA(launch_interp_simt(h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq, h->d_off, lay.n_aux,
@@ -457,10 +475,21 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
     h->stage_ran[kStageMap] = 1;
     ++launches;
     record(h, 3, s);
-    // tensor-core tiles raise one key per frame (d_part[0, L)); CUDA-core tiles
-    // leave one key per (frame, tile)
-    SRP_CUDA(launch_argmax(h->d_part, lay.tc ? 1 : lay.n_tiles, L, d_argmax, d_peak, s),
-             "argmax kernel");
+    if (lay.rescore) {
+        // the maximiser in FP32 among the tiles near the frame's maximum
+        const float2 *psi_fp32 = from_y ? h->d_psi : static_cast<const float2 *>(d_in);
+        SRP_CUDA(launch_rescore(h->mode == SRP_MODE_CONV, h->d_part, lay.n_tiles, lay.J,
+                                lay.J_pad, lay.Q, h->d_xs, lay.xf, h->d_nq, h->d_off, lay.n_aux,
+                                h->d_xi32, lay.S_pad, psi_fp32, lay.K, L, kRescoreDelta,
+                                h->d_rs_fkey, h->d_rs_slots, h->d_rs_count, d_argmax, d_peak,
+                                s),
+                 "argmax re-scoring kernel");
+    } else {
+        // tensor-core tiles raise one key per frame (d_part[0, L)); CUDA-core
+        // tiles leave one key per (frame, tile)
+        SRP_CUDA(launch_argmax(h->d_part, lay.tc ? 1 : lay.n_tiles, L, d_argmax, d_peak, s),
+                 "argmax kernel");
+    }
     h->stage_ran[kStageArgmax] = 1;
     ++launches;
     record(h, 4, s);
@@ -571,6 +600,12 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     SRP_ALLOC(h->d_psi, L.b_psi);
     SRP_ALLOC(h->d_xi, L.b_xi);
     SRP_ALLOC(h->d_xi16, L.b_xi16);
+    SRP_ALLOC(h->d_xi32, L.b_xi32);
+    SRP_ALLOC(h->d_rs_fkey, L.b_rs);  // the slots and the counters follow the frame keys
+    if (L.b_rs) {
+        h->d_rs_slots = h->d_rs_fkey + L.L_pad;
+        h->d_rs_count = reinterpret_cast<int *>(h->d_rs_slots + (size_t)L.L_pad * kRescoreCtas);
+    }
     SRP_ALLOC(h->d_offc, L.b_offc);
     SRP_ALLOC(h->d_xs, L.b_xs);
     SRP_ALLOC(h->d_ctab, L.b_ctab);
@@ -605,7 +640,8 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
         (e = up(h->d_nq, L.Nq.data(), L.b_nq)) != cudaSuccess ||
         (e = up(h->d_off, L.off.data(), L.b_off)) != cudaSuccess ||
         (e = up(h->d_offc, L.offc.data(), L.b_offc)) != cudaSuccess ||
-        (e = cudaMemset(h->d_status, 0, L.b_status)) != cudaSuccess)
+        (e = cudaMemset(h->d_status, 0, L.b_status)) != cudaSuccess ||
+        (L.b_rs && (e = cudaMemset(h->d_rs_fkey, 0, L.b_rs)) != cudaSuccess))
         return bail(cuda_fail(e, "upload pair tables"));
     if (L.b_twid) {
         std::vector<float2> tw(L.K);

@@ -28,6 +28,15 @@ enum Stage { kStagePhat = 0, kStageGcc = 1, kStageMap = 2, kStageArgmax = 3, kNu
 // tolerance of the FP32 maps.
 constexpr double kTcAccumBias = 1.5e-8;
 constexpr double kTcBiasLimit = 5e-5;
+// FP32 re-scoring of reduced-precision maps: tiles whose maximum lies within
+// kRescoreDelta |max| of the frame's maximum are evaluated again in FP32;
+// twice the 1e-2 x peak error bound of BF16/FP16 maps.
+constexpr float kRescoreDelta = 2e-2f;
+// At most this many tiles per frame are re-scored (more: a nearly flat map,
+// which keeps its reduced-precision maximiser).
+constexpr int kRescoreMaxTiles = 64;
+// CTAs per frame that share the re-scoring of its candidates (at most).
+constexpr int kRescoreCtas = 16;
 
 struct Layout {
     int M = 0, Q = 0, K = 0, Kb = 0, n_aux = 0, S = 0, S_pad = 0, max_nq = 0, xf = 0;
@@ -42,14 +51,17 @@ struct Layout {
     int total_steps = 0; // 16-slot steps holding lags, per tile, of all pairs (resident plans)
     std::vector<char> streamed;  // per pair: its weights are resident and streamed
     bool tc = false;    // the Nyquist map runs on the tensor cores
+    bool rescore = false;  // reduced-precision tensor-core plan choosing its maximiser in FP32
     std::vector<int32_t> offc;
     // byte counts of every device buffer, in allocation order
     size_t b_status = 0, b_offc = 0, b_xs = 0, b_ctab = 0, b_w = 0, b_woff = 0;
     size_t b_pairs = 0, b_nq = 0, b_off = 0, b_x = 0, b_twid = 0, b_psi = 0, b_xi = 0,
-           b_xi16 = 0, b_part = 0, b_in_stage = 0, b_maps_stage = 0, b_small_stage = 0;
+           b_xi16 = 0, b_xi32 = 0, b_rs = 0, b_part = 0, b_in_stage = 0, b_maps_stage = 0,
+           b_small_stage = 0;
     size_t total() const {
-        return b_status + b_offc + b_xs + b_ctab + b_w + b_woff + b_pairs + b_nq + b_off + b_x + b_twid + b_psi + b_xi + b_xi16 + b_part +
-               b_in_stage + b_maps_stage + b_small_stage;
+        return b_status + b_offc + b_xs + b_ctab + b_w + b_woff + b_pairs + b_nq + b_off + b_x +
+               b_twid + b_psi + b_xi + b_xi16 + b_xi32 + b_rs + b_part + b_in_stage +
+               b_maps_stage + b_small_stage;
     }
 };
 
@@ -76,6 +88,12 @@ struct srp_plan_s {
     float2 *d_psi = nullptr;       // [L_max][Q][Kb] cross spectra (STFT input only)
     float *d_xi = nullptr;         // [S_pad][L_pad] GCC samples, frames contiguous
     uint16_t *d_xi16 = nullptr;    // [1 or 2][L_pad][Sc] sign-folded GCC samples, 16-bit
+    float *d_xi32 = nullptr;       // [L_pad][S_pad] FP32 GCC samples (Nyquist FP32 re-scoring)
+    // FP32 re-scoring, one allocation: the frames' largest reduced-precision
+    // keys, per (frame, CTA) best keys, per-frame arrival counters
+    unsigned long long *d_rs_fkey = nullptr;   // [L_pad]
+    unsigned long long *d_rs_slots = nullptr;  // [L_pad][kRescoreCtas]
+    int *d_rs_count = nullptr;                 // [L_pad], zero between calls
     int32_t *d_offc = nullptr;     // [Q] first 16-bit lag slot of pair q (a multiple of 64)
     int2 *d_xs = nullptr;          // [Q][J_pad] (fixed-point TDOA, bits of (-1)^x0 sin(pi f)/pi)
     void *d_w = nullptr;           // resident interpolation matrix (resident_weights plans)
@@ -153,26 +171,43 @@ cudaError_t encode_xi_map(void *xi16, int rows, int S_pad, int N, void *map_out)
 // Tensor-core operand kernels: src is the cross spectra psi[L][Q][Kb], or with
 // from_y the STFT frames y[L][M][Kb] (the weighted cross spectra are formed
 // in the kernel).  best (nullable): the L per-frame argmax keys, cleared here.
+// xi32 (nullable): the FP32 samples too, [L_pad][S32] at the pair offsets off.
 cudaError_t launch_gcc_samples_tc(const float2 *src, bool from_y, int M, const int2 *pairs,
                                   int weighting, int L, int Q, int K, const int32_t *nq,
                                   const int32_t *offc, int n_aux, const float2 *twid,
                                   uint16_t *xi16, int L_pad, int S_pad, int fmt,
-                                  unsigned long long *best, cudaStream_t s);
+                                  unsigned long long *best, float *xi32, const int32_t *off,
+                                  int S32, cudaStream_t s);
 int interp_tc_frames_per_cta(int L);
+// frame_keys (nullable, for the FP32 re-scoring): every tile writes its key
+// per frame to part[l][tile] and raises frame_keys[l] (cleared by the operand
+// kernel), instead of raising part[l].
 cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const int4 *ctab,
                              int par1_used, int64_t J_pad, int64_t J, int Q, const int32_t *nq,
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
                              int conv, int K, float *maps, unsigned long long *part, int n_tiles,
                              int *status, const void *w, const int32_t *woff, int tile_steps,
-                             int all_streamed, cudaStream_t s);
+                             int all_streamed, unsigned long long *frame_keys, cudaStream_t s);
 // Plan time: the resident interpolation matrix (operand A) of every tile.
 cudaError_t launch_build_w(const int2 *xs, const int4 *ctab, const int32_t *woff, int n_chunks,
                            int64_t J_pad, int xf, int tile_steps, int n_tiles, int precision,
                            void *w, cudaStream_t s);
+// psi32 (nullable): the weighted cross spectra [L][Q][Kb] in FP32 too.
 cudaError_t launch_conv_operand_tc(const float2 *src, bool from_y, int M, const int2 *pairs,
                                    int weighting, int L, int Q, int K, const int32_t *offc,
                                    uint16_t *b16, int L_pad, int S_pad, int fmt,
-                                   unsigned long long *best, cudaStream_t s);
+                                   unsigned long long *best, float2 *psi32, cudaStream_t s);
+// FP32 re-scoring of reduced-precision maps (srp_rescore.cu): per frame, the
+// tiles whose key is within delta |max| of the frame's largest key are
+// evaluated again in FP32, candidate by candidate: Nyquist from xi32
+// [L_pad][S32] (off, nq, n_aux), conventional from psi [L][Q][Kb] (the
+// weighted cross spectra, a_k / K applied here).  Writes argmax and peak.
+cudaError_t launch_rescore(bool conv, const unsigned long long *part, int n_tiles, int64_t J,
+                           int64_t J_pad, int Q, const int2 *xs, int xf, const int32_t *nq,
+                           const int32_t *off, int n_aux, const float *xi32, int S32,
+                           const float2 *psi, int K, int L, float delta,
+                           const unsigned long long *fkey, unsigned long long *slots, int *count,
+                           int32_t *argmax, float *peak, cudaStream_t s);
 cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,
                           float *peak, cudaStream_t s);
 

@@ -97,8 +97,15 @@ __global__ void __launch_bounds__(128) k_gcc_static(const float2 *__restrict__ p
 std::mutex g_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_psi_scratch on the current device, looked up once per
-// device (host code only sees a host-side stand-in under that name).
+// Largest dynamic shared memory of k_gcc_static: K + K/2 + 1 twiddles and
+// bins at K = 8192.
+constexpr int kGccStaticMaxSmem = (int)sizeof(float2) * (8192 + 4097);
+
+// Per-device set-up, once, under the lock: the device address of
+// g_psi_scratch (host code only sees a host-side stand-in under that name),
+// and k_gcc_static's shared-memory limit raised to the largest size any K
+// needs, so that no later call changes a process-wide kernel attribute
+// while another host thread launches.
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -106,6 +113,9 @@ cudaError_t scratch_address(void **out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_scratch_ptr[dev] == nullptr) {
+        e = cudaFuncSetAttribute(k_gcc_static, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kGccStaticMaxSmem);
+        if (e != cudaSuccess) return e;
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_psi_scratch);
         if (e != cudaSuccess) return e;
@@ -131,8 +141,8 @@ extern "C" SRP_API srp_status srp_gcc_samples_static(int32_t M, int32_t K, int32
         set_error("srp_gcc_samples_static: K must be even and in [4, 8192]");
         return SRP_ERR_INVALID_ARG;
     }
-    if (n_aux < 0 || Nq == nullptr || L < 0) {
-        set_error("srp_gcc_samples_static: bad n_aux, Nq or L");
+    if (n_aux < 0 || Nq == nullptr || L < 0 || L > 65535) {
+        set_error("srp_gcc_samples_static: bad n_aux or Nq, or L outside [0, 65535]");
         return SRP_ERR_INVALID_ARG;
     }
     const int Q = M * (M - 1) / 2, Kb = K / 2 + 1;
@@ -163,23 +173,14 @@ extern "C" SRP_API srp_status srp_gcc_samples_static(int32_t M, int32_t K, int32
     void *scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
     if (e != cudaSuccess) {
-        set_error(std::string("srp_gcc_samples_static: cudaGetSymbolAddress: ") +
-                  cudaGetErrorString(e));
+        set_error(std::string("srp_gcc_samples_static: set-up: ") + cudaGetErrorString(e));
         return SRP_ERR_CUDA;
     }
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
     float2 *psi = static_cast<float2 *>(scratch);
     k_phat_static<<<dim3((Kb + kBins - 1) / kBins, L), 256, 0, cs>>>(
         static_cast<const float2 *>(d_y), M, Kb, Q, t, psi);
-    const size_t smem = sizeof(float2) * (size_t)(K + Kb);
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_gcc_static, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) {
-            set_error(std::string("srp_gcc_samples_static: ") + cudaGetErrorString(e));
-            return SRP_ERR_CUDA;
-        }
-    }
+    const size_t smem = sizeof(float2) * (size_t)(K + Kb);  // <= kGccStaticMaxSmem
     k_gcc_static<<<dim3(Q, L), 128, smem, cs>>>(psi, Q, K, n_aux, t, d_xi, (int)S);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

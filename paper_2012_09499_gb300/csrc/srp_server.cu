@@ -114,11 +114,20 @@ struct Group {  // one stream's requests in one iteration
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t gpu_start = nullptr, gpu_end = nullptr;  // timed: the iteration's GPU interval
     srp_batch batch = nullptr;
     bool busy = false;
     std::vector<Group> groups;
     double t_start = 0.0;
+    int64_t seq = 0;  // iteration number
 };
+
+struct Interval {  // GPU interval of a retired iteration
+    int64_t seq = 0;
+    double t0 = 0.0, t1 = 0.0;
+    bool counted = false;
+};
+constexpr size_t kHistory = 16;  // retired iterations kept for the overlap count
 
 struct StreamInfo {
     srp_plan_s *plan = nullptr;
@@ -150,11 +159,14 @@ struct srp_server_s {
     std::deque<srp_completion> done;
     std::thread worker;
     bool stop = false;
+    bool hold = false;  // srp_server_hold: queue requests, form no iteration
     std::chrono::steady_clock::time_point t0;
     uint64_t next_id = 1;
     int rr = 0;  // round-robin start of iteration forming
     srp_server_stats stats{};
     std::string worker_error;
+    cudaEvent_t gpu_ref = nullptr;  // device time origin of the iteration intervals
+    std::deque<Interval> history;   // the last kHistory retired iterations
 
     double now_ms() const {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
@@ -174,13 +186,24 @@ void server_release(srp_server_s *s) {
     for (Slot &sl : s->slots) {
         if (sl.batch) srp_batch_destroy(sl.batch);
         if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.gpu_start) cudaEventDestroy(sl.gpu_start);
+        if (sl.gpu_end) cudaEventDestroy(sl.gpu_end);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    if (s->gpu_ref) cudaEventDestroy(s->gpu_ref);
     cudaFree(s->d_arena);
     cudaFreeHost(s->h_pinned);
 }
 
-void complete(srp_server_s *s, const Request &r, int status, double t_done) {
+// Iteration of a completed request (all zero when it never ran).
+struct IterInfo {
+    int64_t seq = 0;
+    int32_t streams = 0, frames = 0;
+    double t_gpu0 = 0.0, t_gpu1 = 0.0;
+};
+
+void complete(srp_server_s *s, const Request &r, int status, double t_done,
+              const IterInfo &it = IterInfo()) {
     srp_completion c;
     memset(&c, 0, sizeof c);
     c.request_id = r.id;
@@ -191,6 +214,11 @@ void complete(srp_server_s *s, const Request &r, int status, double t_done) {
     c.t_submit_ms = r.t_submit;
     c.t_start_ms = r.t_start;
     c.t_done_ms = t_done;
+    c.iteration = it.seq;
+    c.iteration_streams = it.streams;
+    c.iteration_frames = it.frames;
+    c.t_gpu_start_ms = it.t_gpu0;
+    c.t_gpu_end_ms = it.t_gpu1;
     s->done.push_back(c);
     if (status == SRP_OK) {
         s->stats.completed += 1;
@@ -212,6 +240,37 @@ void retire(srp_server_s *s) {
         const double t = s->now_ms();
         const int status = q == cudaSuccess ? SRP_OK : SRP_ERR_CUDA;
         if (q != cudaSuccess) s->worker_error = cudaGetErrorString(q);
+        IterInfo it;
+        it.seq = sl.seq;
+        it.streams = (int32_t)sl.groups.size();
+        for (const Group &g : sl.groups) it.frames += g.L;
+        if (status == SRP_OK) {
+            float a = 0.0f, b = 0.0f;
+            if (cudaEventElapsedTime(&a, s->gpu_ref, sl.gpu_start) == cudaSuccess &&
+                cudaEventElapsedTime(&b, s->gpu_ref, sl.gpu_end) == cudaSuccess) {
+                it.t_gpu0 = a;
+                it.t_gpu1 = b;
+                // count this iteration (and an earlier one) once each if their
+                // GPU intervals intersect
+                bool mine = false;
+                for (Interval &h : s->history)
+                    if (h.t0 < it.t_gpu1 && it.t_gpu0 < h.t1) {
+                        mine = true;
+                        if (!h.counted) {
+                            h.counted = true;
+                            s->stats.overlapped_iterations += 1;
+                        }
+                    }
+                if (mine) s->stats.overlapped_iterations += 1;
+                Interval iv;
+                iv.seq = it.seq;
+                iv.t0 = it.t_gpu0;
+                iv.t1 = it.t_gpu1;
+                iv.counted = mine;
+                s->history.push_back(iv);
+                if (s->history.size() > kHistory) s->history.pop_front();
+            }
+        }
         for (Group &g : sl.groups) {
             for (Request &r : g.reqs) {
                 if (status == SRP_OK) {
@@ -220,7 +279,7 @@ void retire(srp_server_s *s) {
                     if (r.h_peak != nullptr)
                         memcpy(r.h_peak, res + align_up(sizeof(int32_t) * r.L), sizeof(float) * r.L);
                 }
-                complete(s, r, status, t);
+                complete(s, r, status, t, it);
                 s->pin.release(r.pin_off, r.pin_bytes);
             }
             s->dev.release(g.dev_off, g.dev_bytes);
@@ -311,6 +370,7 @@ srp_status launch(srp_server_s *s, int k) {
     std::vector<int32_t *> ams(nb, nullptr);
     bool any_batch = false;
     int launches = 0;
+    SRP_CUDA(cudaEventRecord(sl.gpu_start, st), "record iteration start");
     for (Group &g : sl.groups) {
         const StreamInfo &si = s->streams[g.stream];
         int f = 0;
@@ -357,6 +417,7 @@ srp_status launch(srp_server_s *s, int k) {
             f += r.L;
         }
     }
+    SRP_CUDA(cudaEventRecord(sl.gpu_end, st), "record iteration end");
     SRP_CUDA(cudaEventRecord(sl.done, st), "record iteration event");
     std::lock_guard<std::mutex> lk(s->mu);
     s->stats.kernel_launches += launches;
@@ -378,11 +439,14 @@ void worker_main(srp_server_s *s) {
                 k = (int)j;
                 break;
             }
-        if (k >= 0 && pending && form(s, k)) {
+        if (k >= 0 && pending && !(s->hold && !s->stop) && form(s, k)) {
             Slot &sl = s->slots[k];
             sl.busy = true;
             sl.t_start = s->now_ms();
             s->stats.iterations += 1;
+            sl.seq = s->stats.iterations;
+            s->stats.max_iteration_streams =
+                std::max(s->stats.max_iteration_streams, (int32_t)sl.groups.size());
             lk.unlock();
             srp_status st = launch(s, k);
             lk.lock();
@@ -476,7 +540,9 @@ srp_status srp_server_create(const srp_handle *plans, int32_t n, const srp_serve
     s->slots.resize(d->max_inflight);
     for (Slot &sl : s->slots) {
         if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess)
+            (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreate(&sl.gpu_start)) != cudaSuccess ||
+            (e = cudaEventCreate(&sl.gpu_end)) != cudaSuccess)
             return bail(cuda_fail(e, "server stream"));
         if (!s->batched.empty()) {
             srp_status st = srp_batch_create(s->batched.data(), (int32_t)s->batched.size(),
@@ -484,6 +550,11 @@ srp_status srp_server_create(const srp_handle *plans, int32_t n, const srp_serve
             if (st != SRP_OK) return bail(st);
         }
     }
+    // the origin of the iterations' GPU intervals, complete before any iteration
+    if ((e = cudaEventCreate(&s->gpu_ref)) != cudaSuccess ||
+        (e = cudaEventRecord(s->gpu_ref, s->slots[0].stream)) != cudaSuccess ||
+        (e = cudaEventSynchronize(s->gpu_ref)) != cudaSuccess)
+        return bail(cuda_fail(e, "server time origin"));
     s->stats.device_budget_bytes = s->dev.size();
     s->stats.batched_streams = (int32_t)s->batched.size();
     try {
@@ -554,6 +625,16 @@ srp_status srp_server_poll(srp_server s, srp_completion *out, int32_t max, int32
         s->done.pop_front();
     }
     *n_out = k;
+    return SRP_OK;
+}
+
+srp_status srp_server_hold(srp_server s, int32_t hold) {
+    if (s == nullptr) return fail(SRP_ERR_INVALID_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->hold = hold != 0;
+    }
+    s->cv_work.notify_all();
     return SRP_OK;
 }
 

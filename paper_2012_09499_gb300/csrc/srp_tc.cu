@@ -60,12 +60,15 @@ using namespace tc;
 // through the cross-spectrum scratch are skipped.  CTA (0, 0) also clears
 // the per-frame argmax keys that the map kernel's tiles raise with atomicMax.
 // ---------------------------------------------------------------------------
+// With xi32 the FP32 samples xi_q(n) (not sign-folded) also go to
+// xi32[frame][off[q] + t], for the FP32 re-scoring of the maximiser.
 template <int kFmt, bool kFromY>  // kFmt 0: bf16, 1: bf16 hi/lo split, 2: fp16
 __global__ void __launch_bounds__(128) k_gcc_samples_tc(
     const float2 *__restrict__ src, int M, const int2 *__restrict__ pairs, int weighting, int Q,
     int K, const int32_t *__restrict__ nq, const int32_t *__restrict__ offc, int n_aux,
     const float2 *__restrict__ twid, uint16_t *__restrict__ xi16, int L_pad, int S_pad,
-    unsigned long long *__restrict__ best) {
+    unsigned long long *__restrict__ best, float *__restrict__ xi32,
+    const int32_t *__restrict__ off, int S32) {
     extern __shared__ float2 sm[];
     float2 *tw = sm, *ps = sm + K;
     const int q = blockIdx.x, l = blockIdx.y, Kb = K / 2 + 1;
@@ -105,7 +108,9 @@ __global__ void __launch_bounds__(128) k_gcc_samples_tc(
     }
     __syncthreads();
     const int base = offc[q];
+    float *x32 = xi32 != nullptr ? xi32 + (size_t)l * S32 + off[q] : nullptr;
     gcc_row(tw, ps, K, nq[q] + n_aux, [&](int t, int n, float v) {
+        if (x32 != nullptr) x32[t] = v;
         if (n & 1) v = -v;
         const size_t hi = (size_t)l * S_pad + base + t;
         if (kFmt == 2) {
@@ -126,11 +131,13 @@ __global__ void __launch_bounds__(128) k_gcc_samples_tc(
 // Conventional operand B: slot offc[q] + 2k (+1) of row l holds
 // (a_k/K) Re psi_q(k) (and (a_k/K) Im psi_q(k)), as bf16 (hi, lo) or fp16.
 // ---------------------------------------------------------------------------
+// With psi32 the weighted cross spectrum formed from STFT input is also
+// stored in FP32, psi32[frame][q][k], for the FP32 re-scoring.
 template <int kFmt, bool kFromY>  // kFmt 0: bf16, 1: bf16 hi/lo split, 2: fp16
 __global__ void __launch_bounds__(128) k_conv_operand_tc(
     const float2 *__restrict__ src, int M, const int2 *__restrict__ pairs, int weighting, int Q,
     int K, const int32_t *__restrict__ offc, uint16_t *__restrict__ b16, int L_pad, int S_pad,
-    unsigned long long *__restrict__ best) {
+    unsigned long long *__restrict__ best, float2 *__restrict__ psi32) {
     const int Kb = K / 2 + 1;
     const int k = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y, l = blockIdx.z;
     grid_dep_launch();  // the map kernel may start its prologue now
@@ -146,6 +153,7 @@ __global__ void __launch_bounds__(128) k_conv_operand_tc(
             b = unit_phase(b);
         }
         v = times_conj(a, b);
+        if (psi32 != nullptr) psi32[((size_t)l * Q + q) * Kb + k] = v;
     } else {
         v = src[((size_t)l * Q + q) * Kb + k];
     }
@@ -192,6 +200,7 @@ struct TcArgs {
     const int32_t *woff;    // [n_chunks] first 16-slot step of chunk c within a tile's block
     int tile_steps;         // 16-slot steps per 128-candidate tile
     int all_streamed;       // kW with every chunk resident: the generators read no TDOA table
+    unsigned long long *fkey;  // non-null: write part[frame][tile], raise fkey[frame]
 };
 
 // ---------------------------------------------------------------------------
@@ -475,7 +484,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
             }
             const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, 1);
             key = other > key ? other : key;
-            if (h == 0 && fr < n_rows && key != 0ull) atomicMax(a.part + l0 + fr, key);
+            if (h == 0 && fr < n_rows) {
+                if (a.fkey != nullptr) {
+                    a.part[(size_t)(l0 + fr) * a.n_tiles + blockIdx.x] = key;
+                    atomicMax(a.fkey + l0 + fr, key);
+                } else if (key != 0ull) {
+                    atomicMax(a.part + l0 + fr, key);
+                }
+            }
         }
     } else if (warp == kTmaWarp) {
         // ---------------- B loads (GCC samples) ----------------
@@ -668,12 +684,13 @@ cudaError_t launch_gcc_samples_tc(const float2 *src, bool from_y, int M, const i
                                   int weighting, int L, int Q, int K, const int32_t *nq,
                                   const int32_t *offc, int n_aux, const float2 *twid,
                                   uint16_t *xi16, int L_pad, int S_pad, int fmt,
-                                  unsigned long long *best, cudaStream_t s) {
+                                  unsigned long long *best, float *xi32, const int32_t *off,
+                                  int S32, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * (size_t)(K + K / 2 + 1);
     typedef void (*Kern)(const float2 *, int, const int2 *, int, int, int, const int32_t *,
                          const int32_t *, int, const float2 *, uint16_t *, int, int,
-                         unsigned long long *);
+                         unsigned long long *, float *, const int32_t *, int);
     static const Kern kerns[6] = {k_gcc_samples_tc<0, false>, k_gcc_samples_tc<1, false>,
                                   k_gcc_samples_tc<2, false>, k_gcc_samples_tc<0, true>,
                                   k_gcc_samples_tc<1, true>,  k_gcc_samples_tc<2, true>};
@@ -686,24 +703,24 @@ cudaError_t launch_gcc_samples_tc(const float2 *src, bool from_y, int M, const i
         attr[v] = true;
     }
     kerns[v]<<<dim3(Q, L), 128, smem, s>>>(src, M, pairs, weighting, Q, K, nq, offc, n_aux, twid,
-                                           xi16, L_pad, S_pad, best);
+                                           xi16, L_pad, S_pad, best, xi32, off, S32);
     return cudaGetLastError();
 }
 
 cudaError_t launch_conv_operand_tc(const float2 *src, bool from_y, int M, const int2 *pairs,
                                    int weighting, int L, int Q, int K, const int32_t *offc,
                                    uint16_t *b16, int L_pad, int S_pad, int fmt,
-                                   unsigned long long *best, cudaStream_t s) {
+                                   unsigned long long *best, float2 *psi32, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
     const int Kb = K / 2 + 1;
     dim3 grid((Kb + 127) / 128, Q, L);
     typedef void (*Kern)(const float2 *, int, const int2 *, int, int, int, const int32_t *,
-                         uint16_t *, int, int, unsigned long long *);
+                         uint16_t *, int, int, unsigned long long *, float2 *);
     static const Kern kerns[6] = {k_conv_operand_tc<0, false>, k_conv_operand_tc<1, false>,
                                   k_conv_operand_tc<2, false>, k_conv_operand_tc<0, true>,
                                   k_conv_operand_tc<1, true>,  k_conv_operand_tc<2, true>};
     kerns[fmt + (from_y ? 3 : 0)]<<<grid, 128, 0, s>>>(src, M, pairs, weighting, Q, K, offc, b16,
-                                                       L_pad, S_pad, best);
+                                                       L_pad, S_pad, best, psi32);
     return cudaGetLastError();
 }
 
@@ -717,7 +734,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
                              int conv, int K, float *maps, unsigned long long *part, int n_tiles,
                              int *status, const void *w, const int32_t *woff, int tile_steps,
-                             int all_streamed, cudaStream_t s) {
+                             int all_streamed, unsigned long long *frame_keys, cudaStream_t s) {
     // N is the plan's frames per CTA: the height of the tensor map's box.
     if (L == 0) return cudaSuccess;
     if (w != nullptr && conv) return cudaErrorInvalidValue;  // resident A: Nyquist only
@@ -786,6 +803,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.woff = woff;
     a.tile_steps = tile_steps;
     a.all_streamed = (w != nullptr && all_streamed) ? 1 : 0;
+    a.fkey = frame_keys;
     const int grid_y = (L + N - 1) / N;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(xi_map);
     if (conv) {

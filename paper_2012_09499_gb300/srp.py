@@ -40,7 +40,7 @@ class srp_plan_desc(ctypes.Structure):
         ("mode", ctypes.c_int), ("n_aux", ctypes.c_int32), ("precision", ctypes.c_int),
         ("input_kind", ctypes.c_int), ("max_frames", ctypes.c_int32),
         ("host_io", ctypes.c_int32), ("engine", ctypes.c_int), ("weighting", ctypes.c_int),
-        ("resident_fraction", ctypes.c_float),
+        ("resident_fraction", ctypes.c_float), ("argmax", ctypes.c_int),
     ]
 
 
@@ -51,6 +51,7 @@ class srp_plan_info(ctypes.Structure):
         ("S", ctypes.c_int32), ("max_nq", ctypes.c_int32), ("x_frac_bits", ctypes.c_int32),
         ("max_frames", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
         ("device_bytes", ctypes.c_size_t), ("weight_bytes", ctypes.c_size_t),
+        ("argmax_rescored", ctypes.c_int32),
     ]
 
 
@@ -92,8 +93,11 @@ class srp_server_desc(ctypes.Structure):
 class srp_completion(ctypes.Structure):
     _fields_ = [("request_id", ctypes.c_uint64), ("tag", ctypes.c_uint64),
                 ("stream", ctypes.c_int32), ("L", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("iteration_streams", ctypes.c_int32), ("iteration_frames", ctypes.c_int32),
+                ("iteration", ctypes.c_int64),
                 ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
-                ("t_done_ms", ctypes.c_double)]
+                ("t_done_ms", ctypes.c_double), ("t_gpu_start_ms", ctypes.c_double),
+                ("t_gpu_end_ms", ctypes.c_double)]
 
 
 class srp_server_stats(ctypes.Structure):
@@ -101,7 +105,8 @@ class srp_server_stats(ctypes.Structure):
         "submitted", "completed", "frames_completed", "rejected", "timed_out", "failed",
         "iterations", "kernel_launches", "admission_waits", "queued")] + [
         ("device_budget_bytes", ctypes.c_size_t), ("device_bytes_in_use", ctypes.c_size_t),
-        ("device_bytes_peak", ctypes.c_size_t), ("batched_streams", ctypes.c_int32)]
+        ("device_bytes_peak", ctypes.c_size_t), ("batched_streams", ctypes.c_int32),
+        ("max_iteration_streams", ctypes.c_int32), ("overlapped_iterations", ctypes.c_int64)]
 
 
 _lib = None
@@ -151,6 +156,7 @@ def lib():
                                   ctypes.POINTER(ctypes.c_uint64)],
             "srp_server_poll": [vp, vp, i32, ctypes.POINTER(i32), i32],
             "srp_server_get_stats": [vp, ctypes.POINTER(srp_server_stats)],
+            "srp_server_hold": [vp, i32],
             "srp_server_destroy": [vp],
         }
         for name, args in sigs.items():
@@ -201,8 +207,11 @@ def _stream(s):
 
 def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="fp32",
               input_kind="stft", max_frames=64, far_field=False, host_io=False, engine="auto",
-              weighting="phat", resident_weights=False, resident_fraction=None):
-    """Fill an srp_plan_desc; returns (desc, keep-alive arrays)."""
+              weighting="phat", resident_weights=False, resident_fraction=None,
+              argmax="rescore"):
+    """Fill an srp_plan_desc; returns (desc, keep-alive arrays).  argmax:
+    "rescore" (reduced-precision plans choose the maximiser in FP32) or
+    "map" (the reduced-precision map's own first maximiser)."""
     mic = np.ascontiguousarray(mic_xyz, np.float64)
     grid = np.ascontiguousarray(grid_xyz, np.float64)
     d = srp_plan_desc()
@@ -223,6 +232,7 @@ def make_desc(mic_xyz, grid_xyz, fs, c, K, mode="nyquist", n_aux=2, precision="f
     # resident_weights=True streams the whole matrix; resident_fraction a part of it
     d.resident_fraction = float(resident_fraction if resident_fraction is not None
                                 else (1.0 if resident_weights else 0.0))
+    d.argmax = {"rescore": 0, "map": 1}[argmax]
     return d, (mic, grid)
 
 
@@ -401,7 +411,10 @@ def srp_gcc_samples_static(M, K, n_aux, Nq, d_y, L, d_xi, stream=None):
     fn.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                    ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
     fn.restype = ctypes.c_int
-    nq = np.ascontiguousarray(Nq, np.int32)
+    nq = np.ascontiguousarray(Nq, np.int32).reshape(-1)
+    if nq.size != int(M) * (int(M) - 1) // 2:
+        raise ValueError(f"Nq must hold M(M-1)/2 = {int(M) * (int(M) - 1) // 2} lag counts, "
+                         f"got {nq.size}")
     _check(fn(int(M), int(K), int(n_aux), nq.ctypes.data, _ptr(d_y), int(L), _ptr(d_xi),
               _stream(stream)), "srp_gcc_samples_static")
 
@@ -571,8 +584,15 @@ class Server:
             am, pk, mp = self._pending.pop(c.request_id)
             out.append(dict(id=c.request_id, tag=c.tag, stream=c.stream, L=c.L, status=c.status,
                             t_submit=c.t_submit_ms, t_start=c.t_start_ms, t_done=c.t_done_ms,
+                            iteration=c.iteration, iteration_streams=c.iteration_streams,
+                            iteration_frames=c.iteration_frames,
+                            t_gpu_start=c.t_gpu_start_ms, t_gpu_end=c.t_gpu_end_ms,
                             argmax=am, peak=pk, maps=mp))
         return out
+
+    def hold(self, on=True):
+        """Queue submissions without starting iterations (on) or resume (off)."""
+        _check(lib().srp_server_hold(self.handle, 1 if on else 0), "srp_server_hold")
 
     def drain(self, timeout_s=60.0):
         """Poll until every submitted request has finished."""

@@ -124,8 +124,14 @@ def test_footprint_counts_every_buffer():
     d3, keep3 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, engine="cuda_cores")
     Sp = -(-info.S // 64) * 64
     assert srp.srp_plan_footprint(d3) == common + x_tab + 8 * 1024 + 4 * Sp * Lp
-    d4, keep4 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision="bf16")
+    d4, keep4 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision="bf16",
+                      argmax="map")
     assert srp.srp_plan_footprint(d4) == common + 8 * 1024 + tc_tables + 2 * Lp * Sc
+    # re-scoring the maximiser in FP32 keeps the FP32 GCC samples too
+    d6, keep6 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, precision="bf16")
+    assert srp.srp_plan_describe(d6)[0].argmax_rescored == 1
+    rescore = 4 * Lp * Sp + (17 * 8 + 4) * Lp  # FP32 samples, frame keys, slots, counters
+    assert srp.srp_plan_footprint(d6) == common + 8 * 1024 + tc_tables + 2 * Lp * Sc + rescore
     d2, keep2 = _desc(M=8, J=1000, K=1024, max_frames=64, mode="conventional",
                       engine="cuda_cores")
     assert srp.srp_plan_footprint(d2) == common + x_tab
@@ -140,7 +146,7 @@ def test_footprint_counts_every_buffer():
     ("M", 1), ("M", 65), ("K", 7), ("K", 2), ("K", 16384), ("J", 0), ("fs", 0.0),
     ("c", -1.0), ("n_aux", -1), ("max_frames", 0), ("mode", 3), ("precision", 7),
     ("input_kind", 5), ("grid_kind", 4), ("engine", 2), ("host_io", 3), ("host_io", -1),
-    ("weighting", 2),
+    ("weighting", 2), ("argmax", 2), ("argmax", -1),
 ])
 def test_invalid_descriptors_rejected(field, value):
     d, keep = _desc()
@@ -278,3 +284,18 @@ def test_partial_resident_fraction():
         with pytest.raises(srp.SrpError) as e:
             srp.srp_plan_describe(d)
         assert e.value.status == srp.SRP_ERR_INVALID_ARG
+
+
+def test_static_gcc_samples_checks_before_any_cuda_call():
+    """srp_gcc_samples_static validates its arguments on the host: a lag
+    table of the wrong length is refused by the binding, and sizes beyond its
+    limits by the library, before anything touches a device."""
+    with pytest.raises(ValueError):
+        srp.srp_gcc_samples_static(4, 64, 0, np.zeros(5, np.int32), None, 1, None)
+    L = srp.lib()
+    nq = np.zeros(6, np.int32)
+    for M, K, n_aux, frames in [(17, 64, 0, 1), (4, 63, 0, 1), (4, 64, -1, 1), (4, 64, 0, -1),
+                                (4, 64, 0, 65536), (4, 8192, 0, 200)]:
+        args = (M, K, n_aux, nq.ctypes.data if M == 4 else np.zeros(136, np.int32).ctypes.data,
+                None, frames, None, None)
+        assert L.srp_gcc_samples_static(*args) == srp.SRP_ERR_INVALID_ARG, (M, K, frames)

@@ -50,7 +50,7 @@ def check(maps, idx, peak, ref, tol, exact_argmax=True):
     if exact_argmax:
         ridx = np.argmax(ref, axis=1)
         for l in np.nonzero(idx != ridx)[0]:  # documented ties only
-            assert ref[l, ridx[l]] - ref[l, idx[l]] <= 2 * tol * pk[l]
+            assert ref[l, ridx[l]] - ref[l, idx[l]] < tol * pk[l]
     return (err / pk).max()
 
 
@@ -78,7 +78,7 @@ def test_nyquist_batch_matches_oracle(precision):
     batch.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_conventional_batch_matches_oracle(precision):
     # few pairs and bins, so that the FP32 plans run on the tensor cores
     cfgs = [synth.uneven_instance(50 + i, (600, 1500), 6, M=M, K=K)

@@ -420,6 +420,27 @@ def test_approximation_error_small_on_synthetic_scene():
     assert e[1] < e[0] < -15.0
 
 
+def test_approximation_error_closed_forms():
+    """e_appr (Sec. 4, the ratio of the squared-error sum to the map's squared
+    sum, in dB) in closed form: an approximation (1 - a) SRP has error a SRP
+    at every candidate, so e_appr = 20 log10 |a| dB for any map; a single
+    error of size eps at one candidate gives 10 log10(eps^2 / sum_i SRP^2);
+    the value is per frame (row) and does not depend on the map's scale."""
+    rng = np.random.default_rng(17)
+    srp = rng.normal(size=(5, 333))
+    for a in (0.5, 0.1, 1e-3, 2.0, -0.25):
+        e = oracle.e_appr_db(srp, (1.0 - a) * srp)
+        assert e.shape == (5,)
+        np.testing.assert_allclose(e, 20.0 * np.log10(abs(a)), rtol=0, atol=1e-10)
+    # SRP = (3, 4), SRP_appr = (3, 5): one unit error against a squared sum of 25
+    np.testing.assert_allclose(oracle.e_appr_db([3.0, 4.0], [3.0, 5.0]),
+                               [10.0 * np.log10(1.0 / 25.0)], rtol=0, atol=1e-12)
+    rows = oracle.e_appr_db([[3.0, 4.0], [1.0, 0.0]], [[3.0, 5.0], [1.0, 0.1]])
+    np.testing.assert_allclose(rows, [-13.979400086720377, -20.0], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(oracle.e_appr_db(7.0 * srp, 7.0 * (0.9 * srp)),
+                               oracle.e_appr_db(srp, 0.9 * srp), rtol=0, atol=1e-12)
+
+
 def test_argmax_first_maximum():
     """Ties resolve to the lowest candidate index (the first maximiser)."""
     maps = np.array([[0.0, 2.0, 1.0, 2.0], [-1.0, -1.0, -3.0, -1.0], [5.0, 5.0, 5.0, 5.0]])

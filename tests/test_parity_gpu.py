@@ -2,7 +2,7 @@
 
 Tolerance for the FP32 path: max_i |map - oracle| <= 1e-4 x max_i |oracle|
 per frame; argmax equal to the oracle's first maximiser except on documented
-ties (the oracle's value at the GPU's index within twice that bound of the
+ties (the oracle's value at the GPU's index less than that bound below the
 oracle's maximum).  The GPU's argmax must also be the exact first maximiser
 of the GPU's own map, and its peak the exact map value there.
 """
@@ -50,6 +50,19 @@ def check_self_consistent(maps, idx, peak):
     assert np.array_equal(peak, maps[np.arange(L), idx])
 
 
+def check_rescored_argmax(idx, peak, ref):
+    """Reduced-precision plans choose the maximiser in FP32: it is the
+    oracle's first maximiser except on documented FP32 ties, and the peak is
+    the FP32 value there (within the FP32 tolerance)."""
+    pk = np.abs(ref).max(axis=1)
+    rows = np.arange(ref.shape[0])
+    assert np.all(np.abs(peak.astype(np.float64) - ref[rows, idx]) <= TOL_FP32 * pk)
+    ridx = np.argmax(ref, axis=1)
+    for l in np.nonzero(idx != ridx)[0]:
+        gap = ref[l, ridx[l]] - ref[l, idx[l]]
+        assert gap < TOL_FP32 * pk[l], (l, gap / pk[l])
+
+
 def check_against_oracle(maps, idx, ref, tol):
     peak = np.abs(ref).max(axis=1)
     err = np.abs(maps.astype(np.float64) - ref).max(axis=1)
@@ -57,7 +70,7 @@ def check_against_oracle(maps, idx, ref, tol):
     ridx = np.argmax(ref, axis=1)
     for l in np.nonzero(idx != ridx)[0]:  # documented ties only
         gap = ref[l, ridx[l]] - ref[l, idx[l]]
-        assert gap <= 2 * tol * peak[l], (l, gap / peak[l])
+        assert gap < tol * peak[l], (l, gap / peak[l])
     return (err / peak).max()
 
 
@@ -158,7 +171,8 @@ def test_map_cross_spectra_input(mode):
 @pytest.mark.parametrize("mode,engine,precision", [
     ("nyquist", "auto", "fp32"), ("nyquist", "cuda_cores", "fp32"),
     ("nyquist", "auto", "bf16"), ("nyquist", "auto", "fp16"), ("conventional", "auto", "fp32"),
-    ("conventional", "cuda_cores", "fp32"), ("conventional", "auto", "bf16")])
+    ("conventional", "cuda_cores", "fp32"), ("conventional", "auto", "bf16"),
+    ("conventional", "auto", "fp16")])
 def test_map_room_3d_full_size_sampled(mode, engine, precision):
     """The 3D workload at full size (M = 8, J = 480000, K = 1024, L = 64) in
     the launch configuration the benchmark times; the oracle checks sampled
@@ -167,10 +181,13 @@ def test_map_room_3d_full_size_sampled(mode, engine, precision):
     cfg = synth.room_3d(seed=0)
     plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], mode=mode, n_aux=2,
                     max_frames=64, engine=engine, precision=precision)
+    rescored = plan.info.argmax_rescored == 1
+    assert rescored == (precision != "fp32")
     m, a, p = plan.map(dev(cfg["Y"]))
     torch.cuda.synchronize()
     maps, idx, peak = m.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy()
-    check_self_consistent(maps, idx, peak)
+    if not rescored:
+        check_self_consistent(maps, idx, peak)
     rng = np.random.default_rng(0)
     frames = np.array([0, 21, 63])
     cand = np.unique(np.concatenate([rng.choice(cfg["grid"].shape[0], 3000, replace=False),
@@ -187,7 +204,11 @@ def test_map_room_3d_full_size_sampled(mode, engine, precision):
     assert np.all(np.abs(sub - ref).max(axis=1) <= tol * peak_ref)
     # the GPU maximiser is (within tolerance) at least as high as every sampled candidate
     at_idx = np.array([ref[r, np.searchsorted(cand, idx[f])] for r, f in enumerate(frames)])
-    assert np.all(at_idx >= ref.max(axis=1) - 2 * tol * peak_ref)
+    assert np.all(at_idx >= ref.max(axis=1) - tol * peak_ref)
+    if rescored:  # chosen in FP32: as high as every sampled candidate within the FP32 bound,
+        # and the peak is the FP32 value there
+        assert np.all(at_idx >= ref.max(axis=1) - TOL_FP32 * peak_ref)
+        assert np.all(np.abs(peak[frames] - at_idx) <= TOL_FP32 * peak_ref)
 
 
 def test_map_room_3d_full_frame_nyquist():
@@ -322,36 +343,95 @@ def _cell_distance(grid, a, b):
     return np.linalg.norm(grid[a] - grid[b], axis=-1)
 
 
+PRECISION_SEEDS = 40
+
+
 @pytest.mark.parametrize("mode,precision", [("nyquist", "bf16"), ("nyquist", "fp16"),
-                                            ("conventional", "bf16")])
+                                            ("conventional", "bf16"), ("conventional", "fp16")])
 def test_precision_two_sources(mode, precision):
-    """2D array, grid 41 x 41, a second source at -6 dB, 160 frames:
-    max |map - oracle| <= 1e-2 x peak; argmax within one grid cell of the
-    oracle's on >= 99 % of the frames that are not documented ties, and every
-    frame outside one cell is a documented tie (the oracle's map at the GPU's
-    maximiser within twice the bound of the oracle's maximum: the two
-    sources' peaks; 2 of these 160 frames are such ties, for BF16 and FP16
-    alike)."""
-    near, total, ties, worst = 0, 0, 0, 0.0
-    for seed in range(10):
+    """The precision variant of the 2D workload (grid 41 x 41, a second
+    source at -6 dB), 40 seeds x 16 = 640 frames: max |map - oracle| <=
+    1e-2 x peak, and the argmax within one grid cell of the oracle's on at
+    least 99 % of all frames.  The argmax is chosen in FP32 among the tiles
+    near the reduced-precision maximum, so it is in fact the oracle's first
+    maximiser except on documented FP32 ties, with the FP32 value as peak.
+    The map's own maximiser (argmax="map") is not: on broad peaks a
+    candidate two or more cells away is within 1e-4 of the maximum, and BF16
+    rounding moves the maximiser there on about 5 % of these frames."""
+    near, total, worst = 0, 0, 0.0
+    for seed in range(PRECISION_SEEDS):
         cfg = synth.tiny_2d(seed=seed, L=16, second_source_db=-6.0)
         maps, idx, peak = gpu_run(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"],
                                   cfg["Y"], mode, 2, precision=precision)
-        check_self_consistent(maps, idx, peak)
         ref = oracle_maps(cfg, mode, 2)
         pk = np.abs(ref).max(axis=1)
         worst = max(worst, float((np.abs(maps - ref).max(axis=1) / pk).max()))
+        check_rescored_argmax(idx, peak, ref)
         ridx = np.argmax(ref, axis=1)
-        ok = _cell_distance(cfg["grid"], idx, ridx) <= 0.1 * np.sqrt(2) + 1e-9
-        for l in np.nonzero(~ok)[0]:
-            gap = ref[l, ridx[l]] - ref[l, idx[l]]
-            assert gap <= 2 * TOL_HALF * pk[l], (seed, l, gap / pk[l])
-            ties += 1
-        near += int(ok.sum())
+        near += int(np.sum(_cell_distance(cfg["grid"], idx, ridx) <= 0.1 * np.sqrt(2) + 1e-9))
         total += len(idx)
     assert worst <= TOL_HALF, worst
-    # the statistic over frames that are not documented ties
-    assert near >= 0.99 * (total - ties), (near, total, ties)
+    assert total == 16 * PRECISION_SEEDS and near >= 0.99 * total, (near, total)
+
+
+@pytest.mark.parametrize("mode,precision", [("nyquist", "bf16"), ("conventional", "fp16")])
+def test_precision_map_argmax_mode(mode, precision):
+    """argmax="map": a reduced-precision plan reports the first maximiser of
+    its own map and the map value there, and its maps equal those of the
+    re-scoring plan bit for bit."""
+    cfg = synth.tiny_2d(seed=4, L=16, second_source_db=-6.0)
+    args = (cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"])
+    out = {}
+    for am in ("map", "rescore"):
+        plan = srp.Plan(*args, mode=mode, n_aux=2, precision=precision, max_frames=16,
+                        argmax=am)
+        assert plan.info.argmax_rescored == (1 if am == "rescore" else 0)
+        m, a, p = plan.map(dev(cfg["Y"]))
+        torch.cuda.synchronize()
+        out[am] = (m.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy())
+        plan.close()
+    check_self_consistent(*out["map"])
+    assert np.array_equal(out["map"][0], out["rescore"][0])
+
+
+@pytest.mark.parametrize("mode", ["nyquist", "conventional"])
+def test_rescored_argmax_repeatable_at_full_size(mode):
+    """The FP32 re-scoring splits a frame's selected tiles over several CTAs:
+    on the 3D workload at full size, BF16, repeated calls give the same
+    argmax and peak bit for bit, and each frame's argmax is at least as high
+    (in the oracle's map) as the oracle's best over the candidates of the
+    re-scored tiles' neighbourhood, i.e. within the FP32 bound of the
+    oracle's value at the oracle's maximiser among all sampled candidates."""
+    cfg = synth.room_3d(seed=2, L=16)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], mode=mode, n_aux=2,
+                    max_frames=16, precision="bf16")
+    Y = dev(cfg["Y"])
+    runs = []
+    for _ in range(5):
+        m, a, p = plan.map(Y)
+        torch.cuda.synchronize()
+        runs.append((a.cpu().numpy(), p.cpu().numpy()))
+    maps = m.cpu().numpy()
+    plan.close()
+    for a, p in runs[1:]:
+        assert np.array_equal(a, runs[0][0]) and np.array_equal(p, runs[0][1])
+    idx, peak = runs[0]
+    # the oracle on the 4096 candidates of highest BF16 value per frame
+    # (they hold every re-scored tile's maximum) and on the argmax
+    frames = np.arange(0, 16, 5)
+    for f in frames:
+        cand = np.unique(np.concatenate([np.argsort(maps[f])[-4096:], [idx[f]]]))
+        x = oracle.tdoa(cfg["mic"], cfg["grid"][cand], cfg["fs"], cfg["c"])
+        psi = oracle.phat(cfg["Y"][f:f + 1])
+        if mode == "conventional":
+            ref = oracle.conventional(psi, x, cfg["K"])[0]
+        else:
+            Nq, _ = oracle.lag_counts(cfg["mic"], cfg["fs"], cfg["c"])
+            ref = oracle.nyquist(oracle.gcc_samples(psi, Nq, 2, cfg["K"]), Nq, 2, x)[0]
+        pk = np.abs(ref).max()
+        at = ref[np.searchsorted(cand, idx[f])]
+        assert at >= ref.max() - TOL_FP32 * pk, (f, at, ref.max())
+        assert abs(float(peak[f]) - at) <= TOL_FP32 * pk
 
 
 def test_long_conventional_reduction_fp32():
@@ -367,8 +447,13 @@ def test_long_conventional_reduction_fp32():
     for prec, tol in [("fp32", TOL_FP32), ("bf16", TOL_HALF)]:
         maps, idx, peak = gpu_run(mic, grid, 16000.0, 343.0, 2048, Y, "conventional", 0,
                                   precision=prec)
-        check_self_consistent(maps, idx, peak)
-        check_against_oracle(maps, idx, ref, tol)
+        pk = np.abs(ref).max(axis=1)
+        assert np.all(np.abs(maps - ref).max(axis=1) <= tol * pk)
+        if prec == "fp32":
+            check_self_consistent(maps, idx, peak)
+            check_against_oracle(maps, idx, ref, tol)
+        else:  # the maximiser chosen in FP32
+            check_rescored_argmax(idx, peak, ref)
 
 
 def test_host_async_pipeline_matches_host_entry():
@@ -416,10 +501,11 @@ def test_unweighted_cross_spectra_match_oracle(mode, precision):
     tol = TOL_FP32 if precision == "fp32" else TOL_HALF
     if precision == "fp32":
         check_against_oracle(maps, a.cpu().numpy(), ref, tol)
+        check_self_consistent(maps, a.cpu().numpy(), p.cpu().numpy())
     else:
         pk = np.abs(ref).max(axis=1)
         assert np.all(np.abs(maps - ref).max(axis=1) <= tol * pk)
-    check_self_consistent(maps, a.cpu().numpy(), p.cpu().numpy())
+        check_rescored_argmax(a.cpu().numpy(), p.cpu().numpy(), ref)
     plan.close()
 
 
@@ -459,4 +545,4 @@ def test_half_precision_wide_frame_tile(precision):
     ref = oracle_maps(cfg, "nyquist")
     pk = np.abs(ref).max(axis=1)
     assert np.all(np.abs(maps - ref).max(axis=1) <= TOL_HALF * pk)
-    check_self_consistent(maps, idx, peak)
+    check_rescored_argmax(idx, peak, ref)

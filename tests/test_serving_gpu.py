@@ -83,6 +83,58 @@ def test_result_alone_equals_result_in_the_mix():
         assert d["t_submit"] <= d["t_start"] <= d["t_done"]
 
 
+def test_iterations_carry_many_streams_and_overlap_on_the_gpu():
+    """Continuous batching on the device: requests from 8 streams queued
+    together (a hold, then a release) are mapped as iterations that each
+    carry every stream's group, the probe's iteration carries the other
+    streams' groups too, and the next iteration is on the GPU while the
+    previous one still is (their GPU intervals intersect).  The probe's
+    result equals the one it gets alone."""
+    cfgs = mix(15, 8, (20000, 40000), 32)
+    plans = plans_for(cfgs, max_frames=32)
+    srv = srp.Server(plans, device_budget_bytes=2 << 30, host_budget_bytes=512 << 20,
+                     max_inflight=2)
+    probe = cfgs[5]["Y"][16:24]
+    srv.submit(5, probe, tag=1)
+    alone = srv.drain()
+    assert len(alone) == 1 and alone[0]["status"] == srp.SRP_OK
+    for s_ in range(len(cfgs)):  # first launches of every plan before the measured part
+        srv.submit(s_, cfgs[s_]["Y"][:8], tag=3)
+    srv.drain()
+    srv.hold(True)
+    for rnd in range(3):  # 3 x 32 frames per stream: three iterations of 8 groups each
+        for s_ in range(len(cfgs)):
+            for b in range(4):
+                if rnd == 0 and s_ == 5 and b == 2:
+                    srv.submit(5, probe, tag=2)
+                else:
+                    srv.submit(s_, cfgs[s_]["Y"][8 * b:8 * b + 8], tag=10)
+    srv.hold(False)
+    done = srv.drain()
+    st = srv.stats
+    srv.close()
+    assert all(d["status"] == srp.SRP_OK for d in done) and len(done) == 96
+    again = [d for d in done if d["tag"] == 2][0]
+    assert np.array_equal(again["argmax"], alone[0]["argmax"])
+    assert np.array_equal(again["peak"], alone[0]["peak"])
+    # the probe's iteration mapped the other streams' frames in the same launch
+    mates = {d["stream"] for d in done if d["iteration"] == again["iteration"]}
+    assert again["iteration_streams"] == 8 and mates == set(range(8))
+    assert st.max_iteration_streams == 8
+    # two iterations were on the GPU at the same time
+    iv = {}
+    for d in done:
+        iv[d["iteration"]] = (d["t_gpu_start"], d["t_gpu_end"])
+    assert len(iv) >= 3
+    its = sorted(iv)
+    pairs = [(a, b) for a in its for b in its if a < b and
+             iv[a][0] < iv[b][1] and iv[b][0] < iv[a][1]]
+    assert pairs, iv
+    assert st.overlapped_iterations >= 2
+    for a, b in iv.values():
+        assert 0.0 < a < b
+
+
 def group_bytes(cfg, L):
     """Device working set of one group of L frames: input, maps, argmax, peak,
     each rounded up to 256 bytes."""

@@ -55,3 +55,13 @@ def test_static_scratch_rejects_oversize():
     srp.srp_gcc_samples_static(M, K, 0, nq, y, 8, xi)  # 8 frames fit
     torch.cuda.synchronize()
     assert torch.all(xi[:8] == 0)
+
+
+def test_static_scratch_rejects_frame_count_beyond_grid_limit():
+    # M = 2, K = 4: 24 bytes of scratch per frame, so 65536 frames would fit
+    # the array, but the frame index is a grid dimension (at most 65535)
+    y = torch.zeros((1, 2, 3), dtype=torch.complex64, device="cuda")
+    xi = torch.zeros((1, 1), dtype=torch.float32, device="cuda")
+    with pytest.raises(srp.SrpError) as e:
+        srp.srp_gcc_samples_static(2, 4, 0, np.zeros(1, np.int32), y, 65536, xi)
+    assert e.value.status == srp.SRP_ERR_INVALID_ARG
