@@ -201,6 +201,7 @@ struct TcArgs {
     int tile_steps;         // 16-slot steps per 128-candidate tile
     int all_streamed;       // kW with every chunk resident: the generators read no TDOA table
     unsigned long long *fkey;  // non-null: write part[frame][tile], raise fkey[frame]
+    int mma_warps;          // 2: two accumulators fed by two warps; 1: one accumulator
 };
 
 // ---------------------------------------------------------------------------
@@ -257,9 +258,11 @@ __global__ void __launch_bounds__(128) k_build_w(const int2 *__restrict__ xs,
 // 128-byte-swizzled shared-memory tile like B.  kW: A is not generated but
 // streamed from the plan's resident interpolation matrix by bulk copies (no
 // swizzle, one block per 16-slot step) next to B.
-template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false>
-__global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
-                                                           const TcArgs a) {
+// kOcc: CTAs per SM the launch is built for (2, or 4 for the 16-bit formats
+// with one accumulator and 128 TMEM columns per CTA).
+template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false, int kOcc = 2>
+__global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
+                                                              const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // control block, then 1024-aligned stages, then the argmax scratch
     const uint32_t raw = smem_u32(smem_raw);
@@ -297,9 +300,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(full_bar(s), 128 + 1);
-            mbar_init(empty_bar(s), 2);
+            mbar_init(empty_bar(s), (uint32_t)a.mma_warps);
         }
-        mbar_init(accum_bar, 2);
+        mbar_init(accum_bar, (uint32_t)a.mma_warps);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -539,8 +542,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
         // the epilogue adds them.  The parity is that of the running step count
         // over the whole tile, which balances the two chains also when every
         // chunk holds an odd number of steps.
+        // With a.mma_warps == 1 the first MMA warp sums every step into one
+        // accumulator (columns [0, N)) and the second has nothing to do.
         const int par = warp - kMmaWarp0;
-        if (lane == 0) {
+        if (lane == 0 && par < a.mma_warps) {
             const uint32_t dt = tmem + (uint32_t)(par * a.N);
             uint32_t acc = 0;  // the first MMA into the accumulator overwrites it
             int g0 = 0;        // 16-lag steps of the earlier chunks
@@ -564,9 +569,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_interp_tc(const __grid_constant
                     !mbar_wait(full_bar(st), ph, abort_flag, a.status))
                     break;
                 tc_fence_after();
-                const int kk0 = (par + g0) & 1;  // this warp's first step of the chunk
+                const int kstep = a.mma_warps;
+                const int kk0 = kstep == 1 ? 0 : (par + g0) & 1;  // this warp's first step
                 g0 += nk;
-                for (int kk = kk0; kk < nk; kk += 2) {
+                for (int kk = kk0; kk < nk; kk += kstep) {
                     const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
                     const uint32_t ac = (uint32_t)(kk * 8);   // 16 values in 8 TMEM columns
                     if (kTm) {
@@ -629,12 +635,12 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false>
+template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false, int kOcc = 2>
 cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_t smem,
                       cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv, kTm, kW>,
+        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv, kTm, kW, kOcc>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
         if (e != cudaSuccess) return e;
@@ -652,7 +658,7 @@ cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_interp_tc<kSplit, kHalf, kConv, kTm, kW>, map, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_interp_tc<kSplit, kHalf, kConv, kTm, kW, kOcc>, map, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -660,6 +666,10 @@ cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_
 template <bool kSplit, bool kHalf, bool kConv>
 cudaError_t launch_tc_a(const CUtensorMap &map, const TcArgs &a, bool tm, int grid_y, size_t smem,
                         cudaStream_t s) {
+    if constexpr (!kSplit) {
+        if (tm && a.mma_warps == 1)  // four CTAs per SM
+            return launch_tc<kSplit, kHalf, kConv, true, false, 4>(map, a, grid_y, smem, s);
+    }
     return tm ? launch_tc<kSplit, kHalf, kConv, true>(map, a, grid_y, smem, s)
               : launch_tc<kSplit, kHalf, kConv, false>(map, a, grid_y, smem, s);
 }
@@ -763,9 +773,26 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     // Operand A in TMEM when two CTAs per SM keep 2N accumulator columns and at
     // least two A stages (32 columns per part) within 256 columns each.
     const bool tm = w == nullptr && 2 * N + 2 * hs * 32 <= 256;
+    // 16-bit formats with up to 64 frames: one accumulator and two or three A
+    // stages in 128 TMEM columns, so that four CTAs (four independent
+    // generator -> MMA pipelines) share an SM
+    // (one accumulator for every 16-bit plan with up to 64 frames, streamed
+    // weights included, so that a plan's maps do not depend on where its
+    // operand A comes from)
+    const bool one_acc = !split && N <= 64;
+    const bool quad = tm && one_acc;
+    a.mma_warps = one_acc ? 1 : 2;
     int stages;
     size_t smem;
-    if (tm) {
+    if (quad) {
+        stages = std::min(kMaxStages, (128 - N) / 32);
+        a.tmem_cols = 128;
+        a.a_col0 = (uint32_t)N;
+        const size_t stage = (size_t)N * 128;
+        smem = fixed + std::max(stage * (size_t)stages, tile_bytes);
+        // at least 46 KB: no fifth CTA (whose TMEM allocation would wait) on an SM
+        smem = std::max(smem, (size_t)(46 * 1024));
+    } else if (tm) {
         stages = 4;
         while (2 * N + stages * hs * 32 > 256) --stages;
         a.tmem_cols = 256;
@@ -776,7 +803,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
         smem = std::max(smem, (size_t)(78 * 1024));
     } else {
         uint32_t cols = 32;
-        while (cols < (uint32_t)(2 * N)) cols <<= 1;  // two accumulators
+        while (cols < (uint32_t)(a.mma_warps * N)) cols <<= 1;  // one or two accumulators
         a.tmem_cols = cols;
         a.a_col0 = 0;
         const size_t stage = (size_t)hs * (kATile + (uint32_t)N * 128u);
@@ -796,7 +823,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.part = part;
     a.n_tiles = n_tiles;
     a.status = status;
-    a.par1_used = par1_used;
+    a.par1_used = a.mma_warps == 2 ? par1_used : 0;
     a.K = K;
     a.vec_maps = (maps != nullptr && (J % 2) == 0 && (reinterpret_cast<uintptr_t>(maps) & 7) == 0);
     a.w = static_cast<const uint4 *>(w);
