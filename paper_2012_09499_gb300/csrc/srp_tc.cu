@@ -255,9 +255,12 @@ __global__ void __launch_bounds__(128) k_build_w(const int2 *__restrict__ xs,
 
 // kTm: operand A is generated into TMEM (32 columns per 64-slot stage and
 // part) and the MMAs read only B from shared memory; otherwise A is a
-// 128-byte-swizzled shared-memory tile like B.  kW: A is not generated but
-// streamed from the plan's resident interpolation matrix by bulk copies (no
-// swizzle, one block per 16-slot step) next to B.
+// 128-byte-swizzled shared-memory tile like B.  kW: the chunks whose weights
+// are resident in the plan's interpolation matrix are not generated but
+// streamed by bulk copies (no swizzle, one block per 16-slot step) into the
+// stage's shared-memory A region next to B.  kTm and kW together: generated
+// chunks go to TMEM as with kTm alone, streamed chunks are read from shared
+// memory, so on-chip generation and HBM streaming share the work.
 // kOcc: CTAs per SM the launch is built for (2, or 4 for the 16-bit formats
 // with one accumulator and 128 TMEM columns per CTA).
 template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false, int kOcc = 2>
@@ -272,7 +275,9 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + 80);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + 84);
     const uint32_t b_tile = (uint32_t)a.N * 128u;
-    const uint32_t stage_bytes = (kSplit ? 2u : 1u) * ((kTm ? 0u : kATile) + b_tile);
+    // (a shared-memory A region unless A only ever comes from TMEM)
+    constexpr bool kSmemA = !kTm || kW;
+    const uint32_t stage_bytes = (kSplit ? 2u : 1u) * ((kSmemA ? kATile : 0u) + b_tile);
     const uint32_t stage0 = base + 1024u;
     // epilogue tile mt[frame][kMtStride] over the (then idle) stage buffers,
     // then the per-row ring of prefetched (TDOA, sp): xring[slot][row], 8 bytes each
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
     auto a_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes; };
     auto a_lo = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + kATile; };
     auto b_hi = [&](int s) {
-        return stage0 + (uint32_t)s * stage_bytes + (kTm ? 0u : (kSplit ? 2u : 1u) * kATile);
+        return stage0 + (uint32_t)s * stage_bytes + (kSmemA ? (kSplit ? 2u : 1u) * kATile : 0u);
     };
     // operand A of stage s in TMEM: part 0 (hi) then part 1 (lo), 32 columns each
     auto a_tm = [&](int s, int part) {
@@ -331,25 +336,28 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
         float wp = 1.0f, wq = 0.0f;  // conventional: e^{-j 2 pi x / K}
         const float two_k = 2.0f / (float)a.K;
         // (TDOA, sp) of the first kXAhead pairs start streaming in now; pair p
-        // sits in slot p % kXRing.  Pair q + 1 is read from its slot when pair q
-        // starts, one chunk or more ahead of its use, and that read issues the
-        // load of pair q + 1 + kXAhead (one commit group per pair).
+        // sits in slot p % kXRing (kXRingW and kXAheadW for kTm with kW, whose
+        // stages also hold streamed A blocks).  Pair q + 1 is read from its
+        // slot when pair q starts, one chunk or more ahead of its use, and that
+        // read issues the load of pair q + 1 + kXAhead (one commit group per
+        // pair).
         const int ring_q = (kW && a.all_streamed) ? 0 : a.Q;  // pairs whose TDOAs are read
+        constexpr int kRing = (kTm && kW) ? kXRingW : kXRing, kAhead = kRing - 1;
 #pragma unroll
-        for (int k = 0; k < kXAhead; ++k) {
+        for (int k = 0; k < kAhead; ++k) {
             if (k < ring_q)
                 cp_async8(xring + (uint32_t)(k * 128 + r) * 8u, &a.xs[(size_t)k * a.J_pad + i]);
             cp_async_commit();
         }
         int32_t nX, nsp;  // (TDOA, sp) of the next pair to start
         auto read_ring = [&](int p) {
-            cp_async_wait<kXAhead - 1>();  // pair p has landed
+            cp_async_wait<kAhead - 1>();  // pair p has landed
             asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];"
                          : "=r"(nX), "=r"(nsp)
-                         : "r"(xring + (uint32_t)((p % kXRing) * 128 + r) * 8u));
-            const int pn = p + kXAhead;
+                         : "r"(xring + (uint32_t)((p % kRing) * 128 + r) * 8u));
+            const int pn = p + kAhead;
             if (pn < ring_q)
-                cp_async8(xring + (uint32_t)((pn % kXRing) * 128 + r) * 8u,
+                cp_async8(xring + (uint32_t)((pn % kRing) * 128 + r) * 8u,
                           &a.xs[(size_t)pn * a.J_pad + i]);
             cp_async_commit();
         };
@@ -575,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
                 for (int kk = kk0; kk < nk; kk += kstep) {
                     const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
                     const uint32_t ac = (uint32_t)(kk * 8);   // 16 values in 8 TMEM columns
-                    if (kTm) {
+                    if (kTm && !streamed) {
                         mma_f16_ts(dt, tah + ac, dbh + adv, a.idesc, acc);
                         if (kSplit) {
                             mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
@@ -768,11 +776,16 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     const uint32_t ab = half ? 0u : 1u;
     a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
     const int hs = split ? 2 : 1;
-    const size_t fixed = 1024 + 1024 + (size_t)kXRing * 128 * sizeof(int2);
     const size_t tile_bytes = ((size_t)N * kMtStride * sizeof(float) + 1023) / 1024 * 1024;
     // Operand A in TMEM when two CTAs per SM keep 2N accumulator columns and at
-    // least two A stages (32 columns per part) within 256 columns each.
-    const bool tm = w == nullptr && 2 * N + 2 * hs * 32 <= 256;
+    // least two A stages (32 columns per part) within 256 columns each.  With
+    // resident weights, the generated chunks still go to TMEM (unless every
+    // chunk is streamed) and the stages also hold a shared-memory A region.
+    const bool streams = w != nullptr;
+    const bool tm = (!streams || !all_streamed) && 2 * N + 2 * hs * 32 <= 256;
+    const size_t fixed =
+        1024 + 1024 + (size_t)((tm && streams) ? kXRingW : kXRing) * 128 * sizeof(int2);
+    const size_t a_region = streams ? kATile : 0;  // per part
     // 16-bit formats with up to 64 frames: one accumulator and two or three A
     // stages in 128 TMEM columns, so that four CTAs (four independent
     // generator -> MMA pipelines) share an SM
@@ -788,7 +801,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
         stages = std::min(kMaxStages, (128 - N) / 32);
         a.tmem_cols = 128;
         a.a_col0 = (uint32_t)N;
-        const size_t stage = (size_t)N * 128;
+        const size_t stage = a_region + (size_t)N * 128;
         smem = fixed + std::max(stage * (size_t)stages, tile_bytes);
         // at least 46 KB: no fifth CTA (whose TMEM allocation would wait) on an SM
         smem = std::max(smem, (size_t)(46 * 1024));
@@ -797,7 +810,7 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
         while (2 * N + stages * hs * 32 > 256) --stages;
         a.tmem_cols = 256;
         a.a_col0 = (uint32_t)(2 * N);
-        const size_t stage = (size_t)hs * N * 128;
+        const size_t stage = (size_t)hs * (a_region + (size_t)N * 128);
         smem = fixed + std::max(stage * (size_t)stages, tile_bytes);
         // at least 78 KB: no third CTA (whose TMEM allocation would wait) on an SM
         smem = std::max(smem, (size_t)(78 * 1024));
@@ -838,7 +851,15 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
         if (half) return launch_tc_a<false, true, true>(map, a, tm, grid_y, smem, s);
         return launch_tc_a<false, false, true>(map, a, tm, grid_y, smem, s);
     }
-    if (w != nullptr) {
+    if (streams && tm) {  // generated chunks in TMEM, streamed ones from shared memory
+        if (split) return launch_tc<true, false, false, true, true>(map, a, grid_y, smem, s);
+        if (half)
+            return quad ? launch_tc<false, true, false, true, true, 4>(map, a, grid_y, smem, s)
+                        : launch_tc<false, true, false, true, true>(map, a, grid_y, smem, s);
+        return quad ? launch_tc<false, false, false, true, true, 4>(map, a, grid_y, smem, s)
+                    : launch_tc<false, false, false, true, true>(map, a, grid_y, smem, s);
+    }
+    if (streams) {
         if (split) return launch_tc<true, false, false, false, true>(map, a, grid_y, smem, s);
         if (half) return launch_tc<false, true, false, false, true>(map, a, grid_y, smem, s);
         return launch_tc<false, false, false, false, true>(map, a, grid_y, smem, s);

@@ -22,6 +22,7 @@ constexpr uint32_t kATile = 128u * 128u;  // 128 candidates x 64 lags x 2 B
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
 constexpr int kXRing = 8;            // (TDOA, sp) prefetch ring (slots per candidate row)
 constexpr int kXAhead = kXRing - 1;  // pairs in flight ahead of the current one
+constexpr int kXRingW = 4;           // the same ring in the kernel that also streams A blocks
 constexpr int kMtStride = 130;       // floats per frame row of the epilogue tile
 constexpr int kMaxStages = 4;        // pipeline stages the kernels' barrier blocks hold
 
