@@ -147,14 +147,19 @@ typedef struct {
     int32_t x_frac_bits; /* fractional bits of the fixed-point TDOA table */
     int32_t max_frames;
     int32_t tensor_cores; /* 1: the map runs on the tensor cores (tcgen05), 0: CUDA cores.
-                             SRP_ENGINE_AUTO keeps an FP32 plan on CUDA cores when its
-                             reduction is long enough for the tensor-core FP32
-                             accumulation bias (about 1.5e-8 per 16-element step) to
-                             reach half the 1e-4 tolerance */
+                             The tensor cores' FP32 accumulation carries a bias of about
+                             1.5e-8 per 16-element step; an FP32 plan whose reduction is
+                             long enough for it to reach half the 1e-4 tolerance
+                             promotes its accumulators (accum_promotion), or, with more
+                             than 64 frames per call (Nyquist maps, which never need it,
+                             aside), runs on CUDA cores */
     size_t device_bytes;  /* bytes srp_plan allocates on the device */
     size_t weight_bytes;  /* of which the resident interpolation matrix (0 if generated) */
     int32_t argmax_rescored; /* 1: srp_map chooses the maximiser in FP32 (reduced-precision
                                 tensor-core plan with SRP_ARGMAX_RESCORE) */
+    int32_t accum_promotion; /* FP32 conventional maps on the tensor cores: every this many
+                                64-slot chunks of the reduction, the accumulators are added
+                                into FP32 sums and restarted (0: never) */
 } srp_plan_info;
 
 typedef struct srp_plan_s *srp_handle;

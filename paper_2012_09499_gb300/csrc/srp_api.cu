@@ -123,7 +123,20 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
         for (int q = 0; q < lay.Q; ++q) steps += round_up(tc_span(d, lay, q), 16) / 16;
         lay.mma_steps = (int)std::min<int64_t>(steps, INT32_MAX);
         const double adds = 3.0 * (double)steps / 2.0;  // 3 products, 2 accumulators
-        if (d->precision == SRP_PREC_FP32 && adds * kTcAccumBias > kTcBiasLimit) lay.tc = false;
+        if (d->precision == SRP_PREC_FP32 && adds * kTcAccumBias > kTcBiasLimit) {
+            // A long conventional reduction stays on the tensor cores if its
+            // accumulators can be promoted: every kPromoteChunks chunks of 64
+            // slots (4 MMA steps, 3 products, over 2 accumulators) they are
+            // added into FP32 sums and restarted, which bounds the bias of
+            // each partial sum by kPromoteChunks * 6 * kTcAccumBias, a quarter of
+            // the limit.  That needs A in TMEM (at most 64 frames per CTA).
+            const bool can = d->mode == SRP_MODE_CONV &&
+                             interp_tc_frames_per_cta(d->max_frames) <= 64;
+            if (can)
+                lay.promote = kPromoteChunks;
+            else
+                lay.tc = false;
+        }
     }
     if (!lay.tc && d->precision != SRP_PREC_FP32)
         return fail(SRP_ERR_UNSUPPORTED, "BF16/FP16 need the tensor-core engine");
@@ -238,6 +251,7 @@ void fill_info(const Layout &lay, srp_plan_info *info) {
     info->device_bytes = lay.total();
     info->weight_bytes = lay.b_w;
     info->argmax_rescored = lay.rescore ? 1 : 0;
+    info->accum_promotion = lay.promote;
 }
 
 template <typename T>
@@ -462,7 +476,7 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
                                   lay.L_pad, L, h->precision, h->mode == SRP_MODE_CONV ? 1 : 0,
                                   lay.K, d_maps, h->d_part, lay.n_tiles, h->d_status, h->d_w,
                                   h->d_woff, lay.tile_steps, lay.tile_steps == lay.total_steps,
-                                  lay.rescore ? h->d_rs_fkey : nullptr, s),
+                                  lay.rescore ? h->d_rs_fkey : nullptr, lay.promote, s),
                  "tensor-core map kernel");
     } else if (h->mode == SRP_MODE_NYQUIST) {
         SRP_CUDA(launch_interp_simt(h->d_x, lay.J_pad, lay.J, lay.Q, h->d_nq, h->d_off, lay.n_aux,

@@ -1041,6 +1041,10 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         if (!p->lay.tc)
             return fail(SRP_ERR_UNSUPPORTED,
                         "a batch takes tensor-core plans only (this plan runs on CUDA cores)");
+        if (p->lay.promote > 0)
+            return fail(SRP_ERR_UNSUPPORTED,
+                        "a batch takes no plan whose FP32 accumulators need promotion (a long "
+                        "conventional reduction): map it with srp_map");
     }
     DeviceGuard g(p0->device);
     if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plans' device");

@@ -28,6 +28,10 @@ enum Stage { kStagePhat = 0, kStageGcc = 1, kStageMap = 2, kStageArgmax = 3, kNu
 // tolerance of the FP32 maps.
 constexpr double kTcAccumBias = 1.5e-8;
 constexpr double kTcBiasLimit = 5e-5;
+// Chunks per accumulator epoch of promoted FP32 conventional plans:
+// 128 * 6 * kTcAccumBias = 1.15e-5 <= kTcBiasLimit / 4.
+constexpr int kPromoteChunks = 128;
+static_assert(kPromoteChunks * 6 * kTcAccumBias <= kTcBiasLimit / 4, "promotion epoch too long");
 // FP32 re-scoring of reduced-precision maps: tiles whose maximum lies within
 // kRescoreDelta |max| of the frame's maximum are evaluated again in FP32;
 // twice the 1e-2 x peak error bound of BF16/FP16 maps.
@@ -48,6 +52,7 @@ struct Layout {
     int par1_used = 0;  // the tile has two or more 16-slot MMA steps (both accumulators written)
     int mma_steps = 0;   // tensor-core plans: 16-slot MMA steps per tile over all pairs
     int tile_steps = 0;  // resident interpolation matrix: 16-slot steps per tile (0: generated)
+    int promote = 0;     // FP32 conventional on tensor cores: chunks per accumulator epoch (0: none)
     int total_steps = 0; // 16-slot steps holding lags, per tile, of all pairs (resident plans)
     std::vector<char> streamed;  // per pair: its weights are resident and streamed
     bool tc = false;    // the Nyquist map runs on the tensor cores
@@ -187,7 +192,8 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
                              int conv, int K, float *maps, unsigned long long *part, int n_tiles,
                              int *status, const void *w, const int32_t *woff, int tile_steps,
-                             int all_streamed, unsigned long long *frame_keys, cudaStream_t s);
+                             int all_streamed, unsigned long long *frame_keys, int promote,
+                             cudaStream_t s);
 // Plan time: the resident interpolation matrix (operand A) of every tile.
 cudaError_t launch_build_w(const int2 *xs, const int4 *ctab, const int32_t *woff, int n_chunks,
                            int64_t J_pad, int xf, int tile_steps, int n_tiles, int precision,

@@ -202,6 +202,7 @@ struct TcArgs {
     int all_streamed;       // kW with every chunk resident: the generators read no TDOA table
     unsigned long long *fkey;  // non-null: write part[frame][tile], raise fkey[frame]
     int mma_warps;          // 2: two accumulators fed by two warps; 1: one accumulator
+    int promote;            // conventional FP32: chunks per accumulator epoch (0: one epoch)
 };
 
 // ---------------------------------------------------------------------------
@@ -263,17 +264,22 @@ __global__ void __launch_bounds__(128) k_build_w(const int2 *__restrict__ xs,
 // memory, so on-chip generation and HBM streaming share the work.
 // kOcc: CTAs per SM the launch is built for (2, or 4 for the 16-bit formats
 // with one accumulator and 128 TMEM columns per CTA).
-template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false, int kOcc = 2>
+// kPr (FP32 conventional, A in TMEM): the accumulators are promoted every
+// a.promote chunks.
+template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false, int kOcc = 2,
+          bool kPr = false>
 __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_constant__ CUtensorMap tmap,
                                                               const TcArgs a) {
+    static_assert(!kPr || (kConv && kSplit && kTm && !kW), "promotion: FP32 conventional, TMEM A");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // control block, then 1024-aligned stages, then the argmax scratch
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *gbase = smem_raw + (base - raw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase);  // full[kMaxStages], empty[kMaxStages], accum
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + 80);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + 84);
+    // full[kMaxStages], empty[kMaxStages], accum, epoch, drained
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + 8 * (2 * kMaxStages + 3));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const uint32_t b_tile = (uint32_t)a.N * 128u;
     // (a shared-memory A region unless A only ever comes from TMEM)
     constexpr bool kSmemA = !kTm || kW;
@@ -284,10 +290,18 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
     const uint32_t tile_bytes = ((uint32_t)a.N * (uint32_t)kMtStride * 4u + 1023u) & ~1023u;
     const uint32_t xring = base + 1024u + max(stage_bytes * (uint32_t)a.stages, tile_bytes);
     float *mt = reinterpret_cast<float *>(gbase + 1024u);
+    // Accumulator promotion (FP32 conventional maps with long reductions):
+    // every a.promote chunks the generator warps add the TMEM accumulators
+    // into rs[frame][row] (FP32, round to nearest) and the MMAs start them
+    // afresh, so that no accumulator sums more than a.promote chunks.
+    constexpr bool promote = kPr;
+    float *rs = reinterpret_cast<float *>(gbase + (xring - base) + kXRing * 128 * sizeof(int2));
 
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
     auto empty_bar = [&](int s) { return smem_u32(&bars[kMaxStages + s]); };
     const uint32_t accum_bar = smem_u32(&bars[2 * kMaxStages]);
+    const uint32_t epoch_bar = smem_u32(&bars[2 * kMaxStages + 1]);    // the epoch's MMAs done
+    const uint32_t drained_bar = smem_u32(&bars[2 * kMaxStages + 2]);  // accumulators read
     auto a_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes; };
     auto a_lo = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + kATile; };
     auto b_hi = [&](int s) {
@@ -308,6 +322,8 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
             mbar_init(empty_bar(s), (uint32_t)a.mma_warps);
         }
         mbar_init(accum_bar, (uint32_t)a.mma_warps);
+        mbar_init(epoch_bar, (uint32_t)a.mma_warps);
+        mbar_init(drained_bar, 128);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -320,6 +336,8 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
 
     if (warp < 4) {
         const int r = threadIdx.x;
+        if (promote)  // the running sums start at zero (each thread owns its row)
+            for (int j = 0; j < a.N; ++j) rs[j * 128 + r] = 0.0f;
         {
         // ---------------- A generation: one candidate row per thread ----------------
         // (kW: chunks whose weights are resident are streamed by the TMA warp and
@@ -428,6 +446,28 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
             }
             mbar_arrive(full_bar(st));
             cur = nxt;
+            if (promote && c > 0 && c % a.promote == 0) {
+                // the epoch ended with chunk c - 1: once its MMAs are done, add
+                // the accumulators to the running sums and release them
+                const uint32_t eph = (uint32_t)(c / a.promote - 1) & 1u;
+                if (!mbar_wait(epoch_bar, eph, abort_flag, a.status)) break;
+                tc_fence_after();
+                const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+                for (int j0 = 0; j0 < a.N; j0 += 16) {
+                    float v[16];
+                    tmem_ld16(trow + (uint32_t)j0, v);
+                    if (a.par1_used) {
+                        float v1[16];
+                        tmem_ld16(trow + (uint32_t)(a.N + j0), v1);
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) v[jj] += v1[jj];
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) rs[(j0 + jj) * 128 + r] += v[jj];
+                }
+                tc_fence_before();
+                mbar_arrive(drained_bar);
+            }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         }
@@ -448,6 +488,10 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
                 tmem_ld16(trow + (uint32_t)(a.N + j0), v1);
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) v[jj] += v1[jj];
+            }
+            if (promote) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) v[jj] += rs[(j0 + jj) * 128 + r];
             }
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) mt[(j0 + jj) * kMtStride + r] = v[jj];
@@ -573,6 +617,17 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
                 const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
                 const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
                 const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
+                if (promote && c > 0 && c % a.promote == 0) {
+                    // end of an epoch: the generators read the accumulators once
+                    // its MMAs are done; the next MMA into each starts it afresh
+                    mma_commit(epoch_bar);
+                    const uint32_t eph = (uint32_t)(c / a.promote - 1) & 1u;
+                    if (!mbar_try_wait(drained_bar, eph) &&
+                        !mbar_wait(drained_bar, eph, abort_flag, a.status))
+                        break;
+                    tc_fence_after();
+                    acc = 0;
+                }
                 if (!mbar_try_wait(full_bar(st), ph) &&
                     !mbar_wait(full_bar(st), ph, abort_flag, a.status))
                     break;
@@ -643,12 +698,13 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false, int kOcc = 2>
+template <bool kSplit, bool kHalf, bool kConv, bool kTm, bool kW = false, int kOcc = 2,
+          bool kPr = false>
 cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_t smem,
                       cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv, kTm, kW, kOcc>,
+        cudaError_t e = cudaFuncSetAttribute(k_interp_tc<kSplit, kHalf, kConv, kTm, kW, kOcc, kPr>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
         if (e != cudaSuccess) return e;
@@ -666,7 +722,8 @@ cudaError_t launch_tc(const CUtensorMap &map, const TcArgs &a, int grid_y, size_
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_interp_tc<kSplit, kHalf, kConv, kTm, kW, kOcc>, map, a);
+    cudaError_t e =
+        cudaLaunchKernelEx(&cfg, k_interp_tc<kSplit, kHalf, kConv, kTm, kW, kOcc, kPr>, map, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -677,6 +734,9 @@ cudaError_t launch_tc_a(const CUtensorMap &map, const TcArgs &a, bool tm, int gr
     if constexpr (!kSplit) {
         if (tm && a.mma_warps == 1)  // four CTAs per SM
             return launch_tc<kSplit, kHalf, kConv, true, false, 4>(map, a, grid_y, smem, s);
+    } else if constexpr (kConv) {
+        if (tm && a.promote > 0)  // promoted accumulators
+            return launch_tc<kSplit, kHalf, kConv, true, false, 2, true>(map, a, grid_y, smem, s);
     }
     return tm ? launch_tc<kSplit, kHalf, kConv, true>(map, a, grid_y, smem, s)
               : launch_tc<kSplit, kHalf, kConv, false>(map, a, grid_y, smem, s);
@@ -752,7 +812,8 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
                              int n_aux, int xf, int S_pad, int L_pad, int L, int precision,
                              int conv, int K, float *maps, unsigned long long *part, int n_tiles,
                              int *status, const void *w, const int32_t *woff, int tile_steps,
-                             int all_streamed, unsigned long long *frame_keys, cudaStream_t s) {
+                             int all_streamed, unsigned long long *frame_keys, int promote,
+                             cudaStream_t s) {
     // N is the plan's frames per CTA: the height of the tensor map's box.
     if (L == 0) return cudaSuccess;
     if (w != nullptr && conv) return cudaErrorInvalidValue;  // resident A: Nyquist only
@@ -844,6 +905,17 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.tile_steps = tile_steps;
     a.all_streamed = (w != nullptr && all_streamed) ? 1 : 0;
     a.fkey = frame_keys;
+    // accumulator promotion: conventional FP32 only, with A in TMEM; its running
+    // sums take N x 128 floats after the TDOA ring
+    a.promote = (conv && split && tm) ? promote : 0;
+    if (promote > 0 && a.promote == 0) return cudaErrorInvalidConfiguration;
+    if (a.promote > 0) {
+        const size_t need = 1024 + 1024 + std::max((size_t)hs * N * 128 * (size_t)stages,
+                                                   tile_bytes) +
+                            (size_t)kXRing * 128 * sizeof(int2) + (size_t)N * 128 * sizeof(float);
+        smem = std::max(smem, need);
+        if (smem > 113 * 1024) return cudaErrorInvalidConfiguration;  // two CTAs per SM
+    }
     const int grid_y = (L + N - 1) / N;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(xi_map);
     if (conv) {

@@ -51,7 +51,7 @@ class srp_plan_info(ctypes.Structure):
         ("S", ctypes.c_int32), ("max_nq", ctypes.c_int32), ("x_frac_bits", ctypes.c_int32),
         ("max_frames", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
         ("device_bytes", ctypes.c_size_t), ("weight_bytes", ctypes.c_size_t),
-        ("argmax_rescored", ctypes.c_int32),
+        ("argmax_rescored", ctypes.c_int32), ("accum_promotion", ctypes.c_int32),
     ]
 
 

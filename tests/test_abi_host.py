@@ -182,19 +182,26 @@ def test_null_handle_rejected():
 
 
 def test_engine_choice_by_accumulation_bias():
-    """FP32 conventional plans with a long reduction stay on CUDA cores; the
-    benchmark's 3D workload and every Nyquist plan use the tensor cores."""
+    """FP32 conventional plans with a long reduction stay on the tensor cores
+    and promote their accumulators every 128 chunks (with up to 64 frames per
+    call; more frames take the CUDA cores); the benchmark's 3D workload and
+    every Nyquist plan use the tensor cores without promotion."""
     rng = np.random.default_rng(5)
     mic8 = rng.uniform(-0.25, 0.25, (8, 3))
     mic16 = rng.uniform(-0.5, 0.5, (16, 3))
     grid = rng.uniform(0, 5, (100, 3))
-    cases = [(mic8, 1024, "conventional", "fp32", 1), (mic16, 2048, "conventional", "fp32", 0),
-             (mic16, 2048, "conventional", "bf16", 1), (mic16, 2048, "nyquist", "fp32", 1),
-             (mic8, 1024, "nyquist", "fp32", 1)]
-    for mic, K, mode, prec, tc in cases:
+    cases = [(mic8, 1024, "conventional", "fp32", 1, 0), (mic16, 2048, "conventional", "fp32", 1, 128),
+             (mic16, 2048, "conventional", "bf16", 1, 0), (mic16, 2048, "nyquist", "fp32", 1, 0),
+             (mic8, 1024, "nyquist", "fp32", 1, 0)]
+    for mic, K, mode, prec, tc, promo in cases:
         d, keep = srp.make_desc(mic, grid, 16000.0, 343.0, K, mode=mode, precision=prec)
         info, _ = srp.srp_plan_describe(d)
         assert info.tensor_cores == tc, (mic.shape[0], K, mode, prec)
+        assert info.accum_promotion == promo, (mic.shape[0], K, mode, prec)
+    d, keep = srp.make_desc(mic16, grid, 16000.0, 343.0, 2048, mode="conventional",
+                            max_frames=65)
+    info, _ = srp.srp_plan_describe(d)
+    assert info.tensor_cores == 0 and info.accum_promotion == 0
     d, keep = srp.make_desc(mic8, grid, 16000.0, 343.0, 1024, engine="cuda_cores")
     assert srp.srp_plan_describe(d)[0].tensor_cores == 0
 

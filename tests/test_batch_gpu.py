@@ -227,6 +227,17 @@ def test_batch_rejects_mixed_modes_and_cuda_core_plans():
     with pytest.raises(srp.SrpError) as e:
         srp.Batch([a, c])
     assert e.value.status == srp.SRP_ERR_UNSUPPORTED
+    # an FP32 conventional plan whose accumulators are promoted maps on its own
+    long = synth.uneven_instance(77, (500, 800), 4, M=16, K=2048)
+    p1 = srp.Plan(long["mic"], long["grid"], long["fs"], long["c"], long["K"],
+                  mode="conventional", max_frames=4)
+    p2 = make_plans(cfgs[1:], "conventional", "fp32", 4)[0]
+    assert p1.info.accum_promotion > 0 and p2.info.accum_promotion == 0
+    with pytest.raises(srp.SrpError) as e:
+        srp.Batch([p2, p1])
+    assert e.value.status == srp.SRP_ERR_UNSUPPORTED
+    p1.close()
+    p2.close()
     batch = srp.Batch([a])
     with pytest.raises(srp.SrpError) as e:  # more frames than the plan takes
         srp.srp_map_batch(batch.handle, [None], [5], None, [None])

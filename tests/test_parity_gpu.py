@@ -435,18 +435,24 @@ def test_rescored_argmax_repeatable_at_full_size(mode):
 
 
 def test_long_conventional_reduction_fp32():
-    """M = 16 (120 pairs), K = 2048: the FP32 conventional plan takes the exact
-    CUDA-core kernel (its tensor-core accumulation bias would exceed half the
-    tolerance) and meets 1e-4 x peak; BF16 stays on the tensor cores."""
+    """M = 16 (120 pairs), K = 2048: the FP32 conventional plan stays on the
+    tensor cores with its accumulators promoted every 128 chunks (one
+    accumulator summing the whole reduction would carry a bias beyond half the
+    tolerance) and meets 1e-4 x peak; so does the CUDA-core engine; BF16 also
+    runs on the tensor cores."""
     rng = np.random.default_rng(21)
     mic = rng.uniform(-0.5, 0.5, (16, 3)) + np.array([2.5, 2.0, 1.5])
     grid = synth.box_grid((10, 8, 6), 0.5)
     Y = synth.free_field_stft(rng, mic, [np.array([1.0, 3.0, 2.0])], 16000.0, 2048, 3, 10.0)
     cfg = dict(mic=mic, grid=grid, fs=16000.0, c=343.0, K=2048, Y=Y)
     ref = oracle_maps(cfg, "conventional", 0)
-    for prec, tol in [("fp32", TOL_FP32), ("bf16", TOL_HALF)]:
+    d, keep = srp.make_desc(mic, grid, 16000.0, 343.0, 2048, mode="conventional", max_frames=3)
+    info, _ = srp.srp_plan_describe(d)
+    assert info.tensor_cores == 1 and info.accum_promotion == 128
+    for prec, tol, eng in [("fp32", TOL_FP32, "auto"), ("fp32", TOL_FP32, "cuda_cores"),
+                           ("bf16", TOL_HALF, "auto")]:
         maps, idx, peak = gpu_run(mic, grid, 16000.0, 343.0, 2048, Y, "conventional", 0,
-                                  precision=prec)
+                                  precision=prec, engine=eng)
         pk = np.abs(ref).max(axis=1)
         assert np.all(np.abs(maps - ref).max(axis=1) <= tol * pk)
         if prec == "fp32":

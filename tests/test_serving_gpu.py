@@ -188,12 +188,18 @@ def test_deadline_expires_while_queued():
 
 
 def test_unbatched_and_cuda_core_streams():
-    """Streams that are not batched (CUDA-core FP32 conventional plans, or
-    batching off) map with their own srp_map calls; results equal srp_map."""
+    """Streams that are not batched (FP32 conventional plans whose
+    accumulators are promoted, CUDA-core plans, or batching off) map with
+    their own srp_map calls; results equal srp_map."""
     cfgs = [synth.uneven_instance(20 + i, (800, 1500), 8, M=M, K=K)
             for i, (M, K) in enumerate([(12, 2048), (4, 512), (9, 1024)])]
     plans = plans_for(cfgs, mode="conventional", precision="fp32", max_frames=8)
-    assert [p.info.tensor_cores for p in plans] == [0, 1, 0]
+    assert [p.info.tensor_cores for p in plans] == [1, 1, 1]
+    assert [p.info.accum_promotion > 0 for p in plans] == [True, False, True]
+    plans[2].close()  # the third stream on the CUDA cores instead
+    plans[2] = srp.Plan(cfgs[2]["mic"], cfgs[2]["grid"], cfgs[2]["fs"], cfgs[2]["c"],
+                        cfgs[2]["K"], mode="conventional", n_aux=2, precision="fp32",
+                        max_frames=8, engine="cuda_cores")
     for batching in (True, False):
         srv = srp.Server(plans, device_budget_bytes=64 << 20, max_inflight=2,
                          batching=batching)
@@ -207,7 +213,8 @@ def test_unbatched_and_cuda_core_streams():
             m, a, p = plans[s].map(torch.from_numpy(cfgs[s]["Y"][:8]).cuda())
             torch.cuda.synchronize()
             m = m.cpu().numpy()
-            if batching and plans[s].info.tensor_cores:  # the batched kernels
+            if batching and plans[s].info.tensor_cores and not plans[s].info.accum_promotion:
+                # the batched kernels
                 pk = np.abs(m).max(axis=1)
                 assert np.all(np.abs(d["maps"] - m).max(axis=1) <= 1e-6 * pk)
             else:  # the plan's own srp_map call
