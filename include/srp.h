@@ -405,7 +405,8 @@ typedef struct {
                                 [16, 128]; 0 = the largest max_frames rounded up to 16,
                                 at most 64 */
     int32_t stages;          /* operand pipeline depth in [2, 4]; 0 = the most that fit */
-    int32_t ctas_per_sm;     /* persistent CTAs per SM, 1 or 2; 0 = 2 where they fit */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM, 1, 2 or 4 (4: BF16/FP16 with A in
+                                TMEM, 128 TMEM columns per CTA); 0 = the most that fit */
     int32_t operand_a;       /* where the generated operand A lives: 1 = tensor memory
                                 (the MMAs read only B from shared memory), 2 = shared
                                 memory; 0 = tensor memory where it fits */

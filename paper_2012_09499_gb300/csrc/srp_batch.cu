@@ -272,10 +272,12 @@ __device__ __forceinline__ void sync_128() { asm volatile("bar.sync 1, 128;" :::
 // parity), columns [b W N, b W N + W N) for W = mma_warps.
 // ---------------------------------------------------------------------------
 // kTm: operand A is generated into TMEM after the accumulators (32 columns per
-// stage and part) and the MMAs read only B from shared memory.
-template <bool kSplit, bool kHalf, bool kConv, bool kTm>
-__global__ void __launch_bounds__(kThreads, 2) k_map_batch_tc(const __grid_constant__ CUtensorMap tmap,
-                                                              const PersistArgs a) {
+// stage and part) and the MMAs read only B from shared memory.  kOcc: CTAs per
+// SM the registers are sized for (2, or 4 for the 16-bit formats in 128 TMEM
+// columns per CTA).
+template <bool kSplit, bool kHalf, bool kConv, bool kTm, int kOcc = 2>
+__global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_constant__ CUtensorMap tmap,
+                                                                 const PersistArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -725,7 +727,11 @@ uint32_t persist_tmem_cols(const TileChoice &t, bool split) {
 bool tile_fits(const TileChoice &t, bool split, bool any_resident, bool one_acc) {
     if (t.N < 16 || t.N > 256 || (t.N & 15)) return false;
     if (t.tm && any_resident) return false;  // streamed A blocks live in shared memory
-    if (t.stages < 2 || t.stages > kMaxStages || t.cps < 1 || t.cps > 2) return false;
+    if (t.stages < 2 || t.stages > kMaxStages || t.cps < 1 || t.cps > 4 || t.cps == 3)
+        return false;
+    // four CTAs per SM: 16-bit formats with A in TMEM (the register budget of the
+    // FP32 split does not fit)
+    if (t.cps == 4 && (split || !t.tm)) return false;
     if (t.mw < 1 || t.mw > 2 || (t.mw == 1 && !one_acc)) return false;
     if (persist_tmem_cols(t, split) * (uint32_t)t.cps > 512u) return false;
     const size_t smem = persist_smem(t, split);
@@ -941,6 +947,10 @@ srp_status batch_configure(srp_batch_s *b, const TileChoice &t) {
     smem = std::max(smem, ((size_t)kSmemPerSm / (t.cps + 1) - 1024 + 16 + 15) / 16 * 16);
     const bool conv = b->mode == SRP_MODE_CONV;
     void (*persist)(const CUtensorMap, const PersistArgs) =
+        t.cps == 4 ? (conv ? (b->half ? k_map_batch_tc<false, true, true, true, 4>
+                                      : k_map_batch_tc<false, false, true, true, 4>)
+                           : (b->half ? k_map_batch_tc<false, true, false, true, 4>
+                                      : k_map_batch_tc<false, false, false, true, 4>)) :
         t.tm ? (conv ? (b->split ? k_map_batch_tc<true, false, true, true>
                                  : (b->half ? k_map_batch_tc<false, true, true, true>
                                             : k_map_batch_tc<false, false, true, true>))
@@ -1146,7 +1156,7 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
     TileChoice best;
     for (int tm = 1; tm >= 0; --tm) {  // A in TMEM first
         if ((given_a == 1 && !tm) || (given_a == 2 && tm)) continue;
-        for (int cps = 2; cps >= 1; --cps) {
+        for (int cps = 4; cps >= 1; cps = (cps == 4 ? 2 : cps - 1)) {
             if (given_cps && cps != tiles->ctas_per_sm) continue;
             for (int mw = 2; mw >= 1; --mw) {
                 if (given_mw != 0 && mw != given_mw) continue;
@@ -1210,7 +1220,7 @@ srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const int32_t *L
     for (int N : Ns) {
         if (result != SRP_OK) break;
         for (int tm = 0; tm <= 1 && result == SRP_OK; ++tm)
-        for (int cps = 1; cps <= 2 && result == SRP_OK; ++cps)
+        for (int cps = 1; cps <= 4 && result == SRP_OK; cps = (cps == 2 ? 4 : cps + 1))
         for (int mw = 1; mw <= 2 && result == SRP_OK; ++mw)
             for (int stg = 2; stg <= 4 && result == SRP_OK; ++stg) {
                 TileChoice c;
