@@ -116,10 +116,14 @@ __device__ __forceinline__ uint16_t to16(float v, int fmt_half) {
 }
 
 // ---------------------------------------------------------------------------
-// Operand kernel: one CTA per (plan, frame, block of kPairBlock pairs).
+// Operand kernel: one CTA per (plan, frame, block of kPairBlock pairs), of
+// kOpThreads threads (eight warps share a CTA's twiddles and spectrum rows,
+// whose shared memory would otherwise bound the SM to four-warp CTAs).
 // ---------------------------------------------------------------------------
+constexpr int kOpThreads = 256;
+
 template <int kFmt, bool kConv>  // kFmt 0: bf16, 1: bf16 hi/lo split, 2: fp16
-__global__ void __launch_bounds__(128) k_batch_operands(const BatchInst *__restrict__ inst,
+__global__ void __launch_bounds__(kOpThreads) k_batch_operands(const BatchInst *__restrict__ inst,
                                                         const BatchCall *__restrict__ call,
                                                         int n, uint16_t *__restrict__ b16) {
     extern __shared__ float2 sm[];
@@ -824,7 +828,8 @@ cudaError_t enqueue_kernels(srp_batch_s *b, cudaStream_t s, bool timed) {
     const int n = (int)b->plans.size();
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(b->b_map);
     if (timed) cudaEventRecord(b->ev[0], s);
-    b->operands<<<(unsigned)b->op_blocks, 128, b->op_smem, s>>>(b->d_inst, b->d_call, n, b->d_b);
+    b->operands<<<(unsigned)b->op_blocks, kOpThreads, b->op_smem, s>>>(b->d_inst, b->d_call, n,
+                                                                       b->d_b);
     if (timed) cudaEventRecord(b->ev[1], s);
     b->persist<<<(unsigned)b->n_ctas, kThreads, b->persist_smem_bytes, s>>>(map, b->pargs);
     if (timed) cudaEventRecord(b->ev[2], s);
