@@ -36,8 +36,9 @@ METRIC = "SRP cells*pairs/s (Nyquist vs conventional) at stated map error; p50/p
 UNIT = "cells*pairs/s"
 WORKLOAD = dict(name="room_3d", M=8, J=480000, K=1024, L=64, n_aux=2, fs=16000.0, snr_db=10.0)
 FLUSH_BYTES = 256 << 20
-# The kernel sources whose DRAM traffic a recorded ncu capture describes.
-KERNEL_SOURCES = ("srp_tc.cu", "srp_tc_common.cuh", "srp_device.cuh", "srp_batch.cu")
+# The sources of the single-plan tensor-core kernels, whose DRAM traffic a
+# recorded ncu capture describes.
+KERNEL_SOURCES = ("srp_tc.cu", "srp_tc_common.cuh", "srp_device.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
 
