@@ -381,9 +381,9 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
         };
         read_ring(0);
         int4 cur = __ldg(&a.ctab[0]);
+        int st = 0;        // stage of chunk c, and the parity of its use
+        uint32_t ph = 0;
         for (int c = 0; c < a.n_chunks; ++c) {
-            const int st = c % a.stages;
-            const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
             const int4 nxt = __ldg(&a.ctab[c + 1 < a.n_chunks ? c + 1 : c]);
             if (cur.x != q && ring_q > 0) {  // uniform: a new pair starts with this chunk
                 q = cur.x;
@@ -446,6 +446,10 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
             }
             mbar_arrive(full_bar(st));
             cur = nxt;
+            if (++st == a.stages) {
+                st = 0;
+                ph ^= 1u;
+            }
             if (promote && c > 0 && c % a.promote == 0) {
                 // the epoch ended with chunk c - 1: once its MMAs are done, add
                 // the accumulators to the running sums and release them
@@ -553,10 +557,10 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
         if (lane == 0) {
             const uint32_t bytes = (kSplit ? 2u : 1u) * b_tile;
             int issued = 0;
+            int st = 0;  // stage of chunk c, and the parity of its use
+            uint32_t ph = 0;
             grid_dep_wait();  // operand B is written by the previous kernel
             for (int c = 0; c < a.n_chunks; ++c) {
-                const int st = c % a.stages;
-                const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
                 if (c >= a.stages && !mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status))
                     break;
                 if (*abort_flag) break;
@@ -574,6 +578,10 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
                 tma_load_2d(b_hi(st), &tmap, c * kChunk, l0, full_bar(st));
                 if (kSplit) tma_load_2d(b_lo(st), &tmap, c * kChunk, a.L_pad + l0, full_bar(st));
                 issued = c + 1;
+                if (++st == a.stages) {
+                    st = 0;
+                    ph ^= 1u;
+                }
             }
             if (*abort_flag) {
                 // let every copy already issued land before the CTA exits
@@ -596,74 +604,104 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
         // chunk holds an odd number of steps.
         // With a.mma_warps == 1 the first MMA warp sums every step into one
         // accumulator (columns [0, N)) and the second has nothing to do.
+        // The whole warp runs the loop and computes every operand alike (the
+        // TMEM base and the chunk-table entries broadcast from lane 0), and one
+        // elected lane issues the chunk's MMAs and the commits that track them,
+        // in the same elected block.
         const int par = warp - kMmaWarp0;
-        if (lane == 0 && par < a.mma_warps) {
-            const uint32_t dt = tmem + (uint32_t)(par * a.N);
+        if (par < a.mma_warps) {
+            const uint32_t tm = __shfl_sync(0xFFFFFFFFu, tmem, 0);
+            const uint32_t dt = tm + (uint32_t)(par * a.N);
+            const int kstep = a.mma_warps;
             uint32_t acc = 0;  // the first MMA into the accumulator overwrites it
             int g0 = 0;        // 16-lag steps of the earlier chunks
+            int st = 0;        // stage of chunk c, and the parity of its use
+            uint32_t ph = 0;
+            int ep = 0;        // promotion: chunks into the current epoch
+            uint32_t eph = 0;  // promotion: parity of the epoch that ends next
+            bool done = false;
             // the chunk table entry of the next chunk is loaded a chunk ahead,
             // so that its latency overlaps the wait instead of delaying the MMAs
-            int nk_next = __ldg(&a.ctab[0]).w;
-            bool streamed_next = kW && __ldg(&a.woff[0]) >= 0;
+            int nk_next = __shfl_sync(0xFFFFFFFFu, __ldg(&a.ctab[0]).w, 0);
+            bool streamed_next = kW && __shfl_sync(0xFFFFFFFFu, __ldg(&a.woff[0]), 0) >= 0;
             for (int c = 0; c < a.n_chunks; ++c) {
-                const int st = c % a.stages;
-                const uint32_t ph = (uint32_t)(c / a.stages) & 1u;
                 const int nk = nk_next;  // 16-lag steps holding lags of the pair
                 const bool streamed = streamed_next;
                 if (c + 1 < a.n_chunks) {
-                    nk_next = __ldg(&a.ctab[c + 1]).w;
-                    streamed_next = kW && __ldg(&a.woff[c + 1]) >= 0;
+                    nk_next = __shfl_sync(0xFFFFFFFFu, __ldg(&a.ctab[c + 1]).w, 0);
+                    streamed_next =
+                        kW && __shfl_sync(0xFFFFFFFFu, __ldg(&a.woff[c + 1]), 0) >= 0;
                 }
                 const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
                 const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
-                const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
-                if (promote && c > 0 && c % a.promote == 0) {
-                    // end of an epoch: the generators read the accumulators once
-                    // its MMAs are done; the next MMA into each starts it afresh
-                    mma_commit(epoch_bar);
-                    const uint32_t eph = (uint32_t)(c / a.promote - 1) & 1u;
-                    if (!mbar_try_wait(drained_bar, eph) &&
-                        !mbar_wait(drained_bar, eph, abort_flag, a.status))
-                        break;
+                const uint32_t tah = tm + a_tm(st, 0), tal = tm + a_tm(st, 1);
+                if (promote && ep == a.promote) {
+                    // the epoch's MMAs were committed to epoch_bar with its last
+                    // chunk; once the generators have read the accumulators,
+                    // the next MMA into each starts it afresh
+                    bool ok = mbar_try_wait(drained_bar, eph) ||
+                              mbar_wait(drained_bar, eph, abort_flag, a.status);
+                    if (!__all_sync(0xFFFFFFFFu, ok)) break;
                     tc_fence_after();
                     acc = 0;
+                    ep = 0;
+                    eph ^= 1u;
                 }
-                if (!mbar_try_wait(full_bar(st), ph) &&
-                    !mbar_wait(full_bar(st), ph, abort_flag, a.status))
-                    break;
+                bool ok = mbar_try_wait(full_bar(st), ph) ||
+                          mbar_wait(full_bar(st), ph, abort_flag, a.status);
+                if (!__all_sync(0xFFFFFFFFu, ok)) break;
                 tc_fence_after();
-                const int kstep = a.mma_warps;
                 const int kk0 = kstep == 1 ? 0 : (par + g0) & 1;  // this warp's first step
                 g0 += nk;
-                for (int kk = kk0; kk < nk; kk += kstep) {
-                    const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
-                    const uint32_t ac = (uint32_t)(kk * 8);   // 16 values in 8 TMEM columns
-                    if (kTm && !streamed) {
-                        mma_f16_ts(dt, tah + ac, dbh + adv, a.idesc, acc);
-                        if (kSplit) {
-                            mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
-                            mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
-                        }
-                    } else if (streamed) {  // A blocks without swizzle, kAStep bytes per step
-                        const uint64_t wah = smem_desc_none(a_hi(st) + (uint32_t)kk * kAStep);
-                        const uint64_t wal = smem_desc_none(a_lo(st) + (uint32_t)kk * kAStep);
-                        mma_f16(dt, wah, dbh + adv, a.idesc, acc);
-                        if (kSplit) {
-                            mma_f16(dt, wah, dbl + adv, a.idesc, 1);
-                            mma_f16(dt, wal, dbh + adv, a.idesc, 1);
-                        }
-                    } else {
-                        mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
-                        if (kSplit) {
-                            mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
-                            mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
+                ++ep;
+                const bool last = c + 1 == a.n_chunks;
+                const bool epoch_end = promote && ep == a.promote && !last;
+                if (elect_one()) {
+#pragma unroll
+                    for (int s = 0; s < kChunk / 16; ++s) {
+                        const int kk = kk0 + s * kstep;
+                        if (kk >= nk) break;
+                        const uint32_t acc_s = s > 0 ? 1u : acc;
+                        const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes in 16-byte units
+                        const uint32_t ac = (uint32_t)(kk * 8);   // 16 values in 8 TMEM columns
+                        if (kTm && !streamed) {
+                            mma_f16_ts(dt, tah + ac, dbh + adv, a.idesc, acc_s);
+                            if (kSplit) {
+                                mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
+                                mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
+                            }
+                        } else if (streamed) {  // A blocks without swizzle, kAStep bytes per step
+                            const uint64_t wah = smem_desc_none(a_hi(st) + (uint32_t)kk * kAStep);
+                            const uint64_t wal = smem_desc_none(a_lo(st) + (uint32_t)kk * kAStep);
+                            mma_f16(dt, wah, dbh + adv, a.idesc, acc_s);
+                            if (kSplit) {
+                                mma_f16(dt, wah, dbl + adv, a.idesc, 1);
+                                mma_f16(dt, wal, dbh + adv, a.idesc, 1);
+                            }
+                        } else {
+                            mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc_s);
+                            if (kSplit) {
+                                mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
+                                mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
+                            }
                         }
                     }
-                    acc = 1;
+                    mma_commit(empty_bar(st));
+                    if (epoch_end) mma_commit(epoch_bar);
+                    if (last) mma_commit(accum_bar);
                 }
-                mma_commit(empty_bar(st));
+                __syncwarp();
+                if (kk0 < nk) acc = 1;
+                if (last) done = true;
+                if (++st == a.stages) {
+                    st = 0;
+                    ph ^= 1u;
+                }
             }
-            mma_commit(accum_bar);
+            // a loop left early (a wait gave up) still commits, so that the
+            // release of TMEM can wait for whatever MMAs were issued
+            if (!done && elect_one()) mma_commit(accum_bar);
+            __syncwarp();
         }
     }
     __syncwarp();

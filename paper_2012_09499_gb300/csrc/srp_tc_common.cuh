@@ -127,6 +127,18 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
                  : "memory");
 }
 
+// One lane of the (converged) warp is elected.  A tcgen05.mma issued under
+// the elected predicate, with operands the whole warp computed alike, is one
+// instruction of the warp; issued under a plain lane test, the compiler must
+// assume several active lanes with different operands and serialise them.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred = 0;
+    asm volatile(
+        "{ .reg .pred P; elect.sync _|P, 0xffffffff; selp.b32 %0, 1, 0, P; }"
+        : "=r"(pred));
+    return pred != 0;
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
