@@ -459,6 +459,8 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
         };
 
         int g = 0, kx = 0;   // chunks and live items so far
+        int st = 0;          // stage of chunk g, and the parity of its use
+        uint32_t ph = 0;
         int4 prev = make_int4(-1, 0, 0, 0);
         for (int t = it0; t < it1; ++t) {
             const int4 it = a.items[t];
@@ -480,8 +482,6 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
             const float two_k = 2.0f / (float)K;
             int4 cur = __ldg(&ctab[0]);
             for (int c = 0; c < n_chunks; ++c, ++g) {
-                const int st = g % a.stages;
-                const uint32_t ph = (uint32_t)(g / a.stages) & 1u;
                 const int4 nxt = __ldg(&ctab[c + 1 < n_chunks ? c + 1 : c]);
                 if (cur.x != q && !skip_ring) {  // uniform: a new pair starts with this chunk
                     q = cur.x;
@@ -541,6 +541,10 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
                 }
                 mbar_arrive(full_bar(st));
                 cur = nxt;
+                if (++st == a.stages) {
+                    st = 0;
+                    ph ^= 1u;
+                }
             }
             if (prev.x >= 0) epilogue(prev, kx - 1);
             prev = it;
@@ -553,6 +557,8 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
         if (lane == 0) {
             const uint32_t bytes = (kSplit ? 2u : 1u) * b_tile;
             int g = 0, issued = 0;
+            int st = 0;  // stage of chunk g, and the parity of its use
+            uint32_t ph = 0;
             bool ok = true;
             for (int t = it0; t < it1 && ok; ++t) {
                 const int4 it = a.items[t];
@@ -564,8 +570,6 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
                 const int n_chunks = I.n_chunks, Lb = I.Lb;
                 const int64_t r0 = I.b_row0 + it.z;
                 for (int c = 0; c < n_chunks; ++c, ++g) {
-                    const int st = g % a.stages;
-                    const uint32_t ph = (uint32_t)(g / a.stages) & 1u;
                     if (g >= a.stages && !mbar_wait(empty_bar(st), ph ^ 1u, abort_flag, a.status)) {
                         ok = false;
                         break;
@@ -590,6 +594,10 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
                     tma_load_2d(b_hi(st), &tmap, 0, y, full_bar(st));
                     if (kSplit) tma_load_2d(b_lo(st), &tmap, 0, y + Lb, full_bar(st));
                     issued = g + 1;
+                    if (++st == a.stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             if (*abort_flag) {
@@ -605,85 +613,115 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
         }
     } else {
         // ---------------- MMA issue ----------------
+        // The whole warp runs the loop on values broadcast from lane 0 (work
+        // items, plan fields, chunk-table entries, the TMEM base), so that
+        // every branch and every MMA operand is uniform, and one elected lane
+        // issues the chunk's MMAs with the commits that track them.
         const int par = warp - kMmaWarp0, nw = a.mma_warps;
-        if (lane == 0 && par < nw) {
-            int g = 0, kx = 0;
+        if (par < nw) {
+            const uint32_t tm = __shfl_sync(0xFFFFFFFFu, tmem, 0);
+            auto bc = [](int v) { return __shfl_sync(0xFFFFFFFFu, v, 0); };
+            auto bcp = [](const void *p) {
+                return reinterpret_cast<const void *>(
+                    __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(p), 0));
+            };
+            int kx = 0, st = 0;  // live items so far; stage of the next chunk
+            uint32_t ph = 0;     // parity of the stage's use
             bool ok = true;
             for (int t = it0; t < it1 && ok; ++t) {
-                const int4 it = a.items[t];
-                if (!live(it)) {
+                int4 it = a.items[t];
+                it = make_int4(bc(it.x), bc(it.y), bc(it.z), bc(it.w));
+                if (!bc(live(it) ? 1 : 0)) {
                     t += it.w - 1;
                     continue;
                 }
                 const BatchInst &I = a.inst[it.x];
                 const int b = kx & 1;
-                if (!mbar_wait(acc_empty(b), ((uint32_t)(kx >> 1) & 1u) ^ 1u, abort_flag, a.status))
-                    break;
+                const bool e_ok = mbar_wait(acc_empty(b), ((uint32_t)(kx >> 1) & 1u) ^ 1u,
+                                            abort_flag, a.status);
+                if (!__all_sync(0xFFFFFFFFu, e_ok)) break;
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)((b * nw + par) * N);
+                const uint32_t dt = tm + (uint32_t)((b * nw + par) * N);
                 uint32_t acc = 0;  // the item's first MMA overwrites the accumulator
                 int g0 = 0;        // 16-slot steps of the item's earlier chunks
-                const int n_chunks = I.n_chunks;
-                const int4 *ctab = I.ctab;
-                const bool resident = !kConv && !kTm && I.w != nullptr;
+                const int n_chunks = bc(I.n_chunks);
+                const int4 *ctab = reinterpret_cast<const int4 *>(bcp(I.ctab));
+                const bool resident = !kConv && !kTm && bcp(I.w) != nullptr;
+                const int32_t *woff =
+                    resident ? reinterpret_cast<const int32_t *>(bcp(I.woff)) : nullptr;
                 // the next chunk's table entry is loaded a chunk ahead
-                int nk_next = __ldg(&ctab[0]).w;
-                bool streamed_next = resident && __ldg(&I.woff[0]) >= 0;
-                for (int c = 0; c < n_chunks; ++c, ++g) {
-                    const int st = g % a.stages;
-                    const uint32_t ph = (uint32_t)(g / a.stages) & 1u;
+                int nk_next = bc(__ldg(&ctab[0]).w);
+                bool streamed_next = resident && bc(__ldg(&woff[0])) >= 0;
+                for (int c = 0; c < n_chunks; ++c) {
                     const int nk = nk_next;
                     const bool streamed = streamed_next;
                     if (c + 1 < n_chunks) {
-                        nk_next = __ldg(&ctab[c + 1]).w;
-                        streamed_next = resident && __ldg(&I.woff[c + 1]) >= 0;
+                        nk_next = bc(__ldg(&ctab[c + 1]).w);
+                        streamed_next = resident && bc(__ldg(&woff[c + 1])) >= 0;
                     }
                     const uint64_t dah = smem_desc_sw128(a_hi(st)), dbh = smem_desc_sw128(b_hi(st));
                     const uint64_t dal = smem_desc_sw128(a_lo(st)), dbl = smem_desc_sw128(b_lo(st));
-                    const uint32_t tah = tmem + a_tm(st, 0), tal = tmem + a_tm(st, 1);
-                    if (!mbar_try_wait(full_bar(st), ph) &&
-                        !mbar_wait(full_bar(st), ph, abort_flag, a.status)) {
+                    const uint32_t tah = tm + a_tm(st, 0), tal = tm + a_tm(st, 1);
+                    const bool f_ok = mbar_try_wait(full_bar(st), ph) ||
+                                      mbar_wait(full_bar(st), ph, abort_flag, a.status);
+                    if (!__all_sync(0xFFFFFFFFu, f_ok)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     // steps alternate over the nw accumulators by the running
                     // step count of the item (balanced chains)
-                    const int kk0 = (par + g0) % nw;
+                    const int kk0 = nw == 1 ? 0 : (par + g0) & 1;
                     g0 += nk;
-                    for (int kk = kk0; kk < nk; kk += nw) {
-                        const uint64_t adv = (uint64_t)(kk * 2);
-                        const uint32_t ac = (uint32_t)(kk * 8);
-                        if (kTm) {
-                            mma_f16_ts(dt, tah + ac, dbh + adv, a.idesc, acc);
-                            if (kSplit) {
-                                mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
-                                mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
-                            }
-                        } else if (streamed) {  // A blocks without swizzle, kAStep per step
-                            const uint64_t wah = smem_desc_none(a_hi(st) + (uint32_t)kk * kAStep);
-                            const uint64_t wal = smem_desc_none(a_lo(st) + (uint32_t)kk * kAStep);
-                            mma_f16(dt, wah, dbh + adv, a.idesc, acc);
-                            if (kSplit) {
-                                mma_f16(dt, wah, dbl + adv, a.idesc, 1);
-                                mma_f16(dt, wal, dbh + adv, a.idesc, 1);
-                            }
-                        } else {
-                            mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc);
-                            if (kSplit) {
-                                mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
-                                mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
+                    const bool last = c + 1 == n_chunks;
+                    if (elect_one()) {
+#pragma unroll
+                        for (int s = 0; s < kChunk / 16; ++s) {
+                            const int kk = kk0 + s * nw;
+                            if (kk >= nk) break;
+                            const uint32_t acc_s = s > 0 ? 1u : acc;
+                            const uint64_t adv = (uint64_t)(kk * 2);
+                            const uint32_t ac = (uint32_t)(kk * 8);
+                            if (kTm) {
+                                mma_f16_ts(dt, tah + ac, dbh + adv, a.idesc, acc_s);
+                                if (kSplit) {
+                                    mma_f16_ts(dt, tah + ac, dbl + adv, a.idesc, 1);
+                                    mma_f16_ts(dt, tal + ac, dbh + adv, a.idesc, 1);
+                                }
+                            } else if (streamed) {  // A blocks without swizzle, kAStep per step
+                                const uint64_t wah = smem_desc_none(a_hi(st) + (uint32_t)kk * kAStep);
+                                const uint64_t wal = smem_desc_none(a_lo(st) + (uint32_t)kk * kAStep);
+                                mma_f16(dt, wah, dbh + adv, a.idesc, acc_s);
+                                if (kSplit) {
+                                    mma_f16(dt, wah, dbl + adv, a.idesc, 1);
+                                    mma_f16(dt, wal, dbh + adv, a.idesc, 1);
+                                }
+                            } else {
+                                mma_f16(dt, dah + adv, dbh + adv, a.idesc, acc_s);
+                                if (kSplit) {
+                                    mma_f16(dt, dah + adv, dbl + adv, a.idesc, 1);
+                                    mma_f16(dt, dal + adv, dbh + adv, a.idesc, 1);
+                                }
                             }
                         }
-                        acc = 1;
+                        mma_commit(empty_bar(st));
+                        if (last) mma_commit(acc_full(b));
                     }
-                    mma_commit(empty_bar(st));
+                    __syncwarp();
+                    if (kk0 < nk) acc = 1;
+                    if (++st == a.stages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (!ok) break;
-                mma_commit(acc_full(b));
+                if (n_chunks == 0 && elect_one()) mma_commit(acc_full(b));  // (no plan has none)
+                __syncwarp();
                 ++kx;
             }
-            mma_commit(drain);  // arrives once every MMA issued above has completed
+            // arrives once every MMA issued above has completed
+            if (elect_one()) mma_commit(drain);
+            __syncwarp();
         }
     }
     __syncwarp();
