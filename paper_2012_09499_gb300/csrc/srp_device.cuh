@@ -21,9 +21,10 @@ __device__ __forceinline__ unsigned long long argmax_key(float v, uint32_t i) {
 
 // The upper half of argmax_key: an unsigned value in the order of v.
 __device__ __forceinline__ uint32_t ordered_value(float v) {
-    if (v == 0.0f) v = 0.0f;
-    const uint32_t u = __float_as_uint(v);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    // -0 + 0 = +0 (round to nearest), so both zeros map alike; negative
+    // values are complemented, non-negative ones get the top bit
+    const uint32_t u = __float_as_uint(v + 0.0f);
+    return u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u);
 }
 
 __device__ __forceinline__ float key_value(unsigned long long k) {

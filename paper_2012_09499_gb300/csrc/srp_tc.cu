@@ -530,11 +530,26 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
                 int bk = -1;
                 const float *row_p = mt + fr * kMtStride;
                 const int kmax = (int)min((int64_t)128, a.J - tile0);
-                for (int k = h; k < kmax; k += 2) {
-                    const uint32_t o = ordered_value(row_p[k]);
-                    if (bk < 0 || o > bo) {
-                        bo = o;
-                        bk = k;
+                if (kmax == 128) {  // full tile: 64 candidates per thread, unrolled
+                    const float *rp = row_p + h;
+                    int bj = 0;
+                    bo = ordered_value(rp[0]);
+#pragma unroll
+                    for (int j = 1; j < 64; ++j) {
+                        const uint32_t o = ordered_value(rp[2 * j]);
+                        if (o > bo) {
+                            bo = o;
+                            bj = j;
+                        }
+                    }
+                    bk = h + 2 * bj;
+                } else {
+                    for (int k = h; k < kmax; k += 2) {
+                        const uint32_t o = ordered_value(row_p[k]);
+                        if (bk < 0 || o > bo) {
+                            bo = o;
+                            bk = k;
+                        }
                     }
                 }
                 if (bk >= 0)
