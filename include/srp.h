@@ -394,8 +394,12 @@ SRP_API srp_status srp_refiner_destroy(srp_refiner r);
  * operand buffer, argmax partials, work list and graph, so the plans stay
  * usable by srp_map.  All plans must be on one device, share mode and
  * precision, and run on the tensor cores (srp_plan_info.tensor_cores == 1);
- * otherwise srp_batch_create returns SRP_ERR_UNSUPPORTED.  Calls on one batch
- * share its buffers and must be ordered, like calls on one plan.
+ * otherwise srp_batch_create returns SRP_ERR_UNSUPPORTED.  FP32 conventional
+ * plans that promote their accumulators (srp_plan_info.accum_promotion > 0)
+ * promote them in the batch too, every accum_promotion chunks; a batch that
+ * holds such a plan keeps operand A in tensor memory and at most two CTAs per
+ * SM.  Calls on one batch share its buffers and must be ordered, like calls on
+ * one plan.
  * ------------------------------------------------------------------------ */
 typedef struct srp_batch_s *srp_batch;
 
@@ -414,8 +418,9 @@ typedef struct {
                                 each summing every other 16-slot step into its own
                                 accumulator (the epilogue adds the two); 1 = one warp and
                                 one accumulator (half the TMEM columns), refused for an
-                                FP32 batch whose longest reduction would accumulate a
-                                TMEM rounding bias above 5e-5 in one accumulator; 0 = 2
+                                FP32 batch whose longest reduction (per promotion epoch,
+                                for a promoted plan) would accumulate a TMEM rounding
+                                bias above 5e-5 in one accumulator; 0 = 2
                                 where the tile fits, else 1 */
 } srp_batch_tiles;
 

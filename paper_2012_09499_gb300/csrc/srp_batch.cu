@@ -67,6 +67,7 @@ struct BatchInst {
     int tile_steps;           // 16-slot steps per tile of w
     int all_streamed;         // every chunk's weights are resident: no TDOA table reads
     int pblocks;              // pair blocks of kPairBlock per frame
+    int promote;              // FP32 conventional: chunks per accumulator epoch (0: one epoch)
     int64_t op_row0;          // first block of the plan in the operand kernel's grid
     int64_t frame0;           // first block of the plan in the argmax kernel's grid
 };
@@ -279,9 +280,15 @@ __device__ __forceinline__ void sync_128() { asm volatile("bar.sync 1, 128;" :::
 // stage and part) and the MMAs read only B from shared memory.  kOcc: CTAs per
 // SM the registers are sized for (2, or 4 for the 16-bit formats in 128 TMEM
 // columns per CTA).
-template <bool kSplit, bool kHalf, bool kConv, bool kTm, int kOcc = 2>
+// kPr (FP32 conventional, A in TMEM): items of plans with I.promote > 0 have
+// their accumulators promoted every I.promote chunks into per-row FP32 sums
+// rs[frame][row] in shared memory (as in the single-plan kernel), and run
+// their epilogue right after their own chunks, so that one set of sums serves
+// every item.
+template <bool kSplit, bool kHalf, bool kConv, bool kTm, int kOcc = 2, bool kPr = false>
 __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_constant__ CUtensorMap tmap,
                                                                  const PersistArgs a) {
+    static_assert(!kPr || (kConv && kSplit && kTm), "promotion: FP32 conventional, TMEM A");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -297,13 +304,16 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
     const uint32_t xring = stage0 + stage_bytes * (uint32_t)a.stages;
     float *mt = reinterpret_cast<float *>(gbase + 1024u + stage_bytes * (uint32_t)a.stages +
                                           (uint32_t)kXRing * 128u * 8u);
+    float *rs = mt + (size_t)N * kMtStride;  // kPr: running sums of the promoted item
 
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
     auto empty_bar = [&](int s) { return smem_u32(&bars[kMaxStages + s]); };
     auto acc_full = [&](int b) { return smem_u32(&bars[2 * kMaxStages + b]); };
     auto acc_empty = [&](int b) { return smem_u32(&bars[2 * kMaxStages + 2 + b]); };
     const uint32_t drain = smem_u32(&bars[2 * kMaxStages + 4]);
-    static_assert((2 * kMaxStages + 5) * 8 <= 128, "barrier block overlaps the TMEM slot");
+    const uint32_t epoch_bar = smem_u32(&bars[2 * kMaxStages + 5]);    // kPr: the epoch's MMAs done
+    const uint32_t drained_bar = smem_u32(&bars[2 * kMaxStages + 6]);  // kPr: accumulators read
+    static_assert((2 * kMaxStages + 7) * 8 <= 128, "barrier block overlaps the TMEM slot");
     auto a_hi = [&](int s) { return stage0 + (uint32_t)s * stage_bytes; };
     auto a_lo = [&](int s) { return stage0 + (uint32_t)s * stage_bytes + kATile; };
     auto b_hi = [&](int s) {
@@ -328,6 +338,8 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
             mbar_init(acc_empty(b), 128);
         }
         mbar_init(drain, a.mma_warps);
+        mbar_init(epoch_bar, a.mma_warps);
+        mbar_init(drained_bar, 128);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -406,6 +418,10 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) v[jj] += v1[jj];
                 }
+                if (kPr && I.promote > 0) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) v[jj] += rs[(j0 + jj) * 128 + r];
+                }
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) mt[(j0 + jj) * kMtStride + r] = v[jj];
             }
@@ -476,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
         int g = 0, kx = 0;   // chunks and live items so far
         int st = 0;          // stage of chunk g, and the parity of its use
         uint32_t ph = 0;
+        uint32_t epar = 0;   // kPr: parity of the next accumulator epoch to end
         int4 prev = make_int4(-1, 0, 0, 0);
         for (int t = it0; t < it1; ++t) {
             const int4 it = a.items[t];
@@ -495,6 +512,10 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
             float wp = 1.0f, wq = 0.0f;
             const int K = I.K;
             const float two_k = 2.0f / (float)K;
+            const int prom = kPr ? I.promote : 0;
+            if (prom > 0)  // the running sums start at zero (each thread owns its row)
+                for (int j = 0; j < N; ++j) rs[j * 128 + r] = 0.0f;
+            bool drained_ok = true;
             int4 cur = __ldg(&ctab[0]);
             for (int c = 0; c < n_chunks; ++c, ++g) {
                 const int4 nxt = __ldg(&ctab[c + 1 < n_chunks ? c + 1 : c]);
@@ -560,9 +581,41 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
                     st = 0;
                     ph ^= 1u;
                 }
+                if (prom > 0 && c > 0 && c % max(prom, 1) == 0) {
+                    // the epoch ended with chunk c - 1: once its MMAs are done,
+                    // add the item's accumulators to the running sums and
+                    // release them
+                    if (!mbar_wait(epoch_bar, epar, abort_flag, a.status)) {
+                        drained_ok = false;
+                        break;
+                    }
+                    epar ^= 1u;
+                    tc_fence_after();
+                    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) +
+                                          (uint32_t)((kx & 1) * a.mma_warps * N);
+                    for (int j0 = 0; j0 < N; j0 += 16) {
+                        float v[16];
+                        tmem_ld16(trow + (uint32_t)j0, v);
+                        if (a.mma_warps == 2 && I.par1_used) {
+                            float v1[16];
+                            tmem_ld16(trow + (uint32_t)(N + j0), v1);
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) v[jj] += v1[jj];
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) rs[(j0 + jj) * 128 + r] += v[jj];
+                    }
+                    tc_fence_before();
+                    mbar_arrive(drained_bar);
+                }
             }
+            if (kPr && !and_128(drained_ok)) break;
             if (prev.x >= 0) epilogue(prev, kx - 1);
             prev = it;
+            if (prom > 0) {  // its sums are needed by no later item: finish it now
+                epilogue(it, kx);
+                prev = make_int4(-1, 0, 0, 0);
+            }
             ++kx;
         }
         if (prev.x >= 0) epilogue(prev, kx - 1);
@@ -642,6 +695,7 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
             };
             int kx = 0, st = 0;  // live items so far; stage of the next chunk
             uint32_t ph = 0;     // parity of the stage's use
+            uint32_t eph = 0;    // kPr: parity of the next epoch drain
             bool ok = true;
             for (int t = it0; t < it1 && ok; ++t) {
                 int4 it = a.items[t];
@@ -664,12 +718,29 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
                 const bool resident = !kConv && !kTm && bcp(I.w) != nullptr;
                 const int32_t *woff =
                     resident ? reinterpret_cast<const int32_t *>(bcp(I.woff)) : nullptr;
+                const int prom = kPr ? bc(I.promote) : 0;
+                int ep = 0;  // chunks into the current accumulator epoch
                 // the next chunk's table entry is loaded a chunk ahead
                 int nk_next = bc(__ldg(&ctab[0]).w);
                 bool streamed_next = resident && bc(__ldg(&woff[0])) >= 0;
                 for (int c = 0; c < n_chunks; ++c) {
                     const int nk = nk_next;
                     const bool streamed = streamed_next;
+                    if (prom > 0 && ep == prom) {
+                        // the epoch's MMAs were committed to epoch_bar with its
+                        // last chunk; once the generators have read the
+                        // accumulators, the next MMA into each starts it afresh
+                        const bool d_ok = mbar_try_wait(drained_bar, eph) ||
+                                          mbar_wait(drained_bar, eph, abort_flag, a.status);
+                        if (!__all_sync(0xFFFFFFFFu, d_ok)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        eph ^= 1u;
+                        acc = 0;
+                        ep = 0;
+                    }
                     if (c + 1 < n_chunks) {
                         nk_next = bc(__ldg(&ctab[c + 1]).w);
                         streamed_next = resident && bc(__ldg(&woff[c + 1])) >= 0;
@@ -688,7 +759,9 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
                     // step count of the item (balanced chains)
                     const int kk0 = nw == 1 ? 0 : (par + g0) & 1;
                     g0 += nk;
+                    ++ep;
                     const bool last = c + 1 == n_chunks;
+                    const bool epoch_end = prom > 0 && ep == prom && !last;
                     if (elect_one()) {
 #pragma unroll
                         for (int s = 0; s < kChunk / 16; ++s) {
@@ -720,6 +793,7 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
                             }
                         }
                         mma_commit(empty_bar(st));
+                        if (epoch_end) mma_commit(epoch_bar);
                         if (last) mma_commit(acc_full(b));
                     }
                     __syncwarp();
@@ -764,10 +838,12 @@ struct TileChoice {
     int mw = 2;       // MMA-issuing warps = accumulators per item
 };
 
-// Bytes of shared memory of the persistent kernel for a tile choice.
-size_t persist_smem(const TileChoice &t, bool split) {
+// Bytes of shared memory of the persistent kernel for a tile choice (with
+// promote, the running sums of a promoted item after the epilogue tile).
+size_t persist_smem(const TileChoice &t, bool split, bool promote) {
     const size_t stage = (split ? 2 : 1) * ((t.tm ? 0 : (size_t)kATile) + (size_t)t.N * 128);
-    return 2048 + stage * t.stages + (size_t)kXRing * 128 * 8 + (size_t)t.N * kMtStride * 4;
+    return 2048 + stage * t.stages + (size_t)kXRing * 128 * 8 + (size_t)t.N * kMtStride * 4 +
+           (promote ? (size_t)t.N * 128 * 4 : 0);
 }
 
 // TMEM columns: two accumulator sets of mw accumulators (2 mw N) and, with A
@@ -781,9 +857,10 @@ uint32_t persist_tmem_cols(const TileChoice &t, bool split) {
     return cols;
 }
 
-bool tile_fits(const TileChoice &t, bool split, bool any_resident, bool one_acc) {
+bool tile_fits(const TileChoice &t, bool split, bool any_resident, bool one_acc, bool promote) {
     if (t.N < 16 || t.N > 256 || (t.N & 15)) return false;
     if (t.tm && any_resident) return false;  // streamed A blocks live in shared memory
+    if (promote && (!t.tm || t.cps > 2)) return false;  // the promoting kernel: A in TMEM
     if (t.stages < 2 || t.stages > kMaxStages || t.cps < 1 || t.cps > 4 || t.cps == 3)
         return false;
     // four CTAs per SM: 16-bit formats with A in TMEM (the register budget of the
@@ -791,7 +868,7 @@ bool tile_fits(const TileChoice &t, bool split, bool any_resident, bool one_acc)
     if (t.cps == 4 && (split || !t.tm)) return false;
     if (t.mw < 1 || t.mw > 2 || (t.mw == 1 && !one_acc)) return false;
     if (persist_tmem_cols(t, split) * (uint32_t)t.cps > 512u) return false;
-    const size_t smem = persist_smem(t, split);
+    const size_t smem = persist_smem(t, split, promote);
     if (smem > (size_t)kMaxSmemCta) return false;
     return (smem + 1024) * (size_t)t.cps <= (size_t)kSmemPerSm;
 }
@@ -813,6 +890,7 @@ struct srp_batch_s {
     int max_L = 0, max_K = 0;
     bool any_resident = false;  // some plan streams its interpolation matrix: A in shared memory
     bool one_acc = true;        // one accumulator per item keeps the FP32 bias within its limit
+    bool promote = false;       // some plan's FP32 accumulators are promoted (long conventional sums)
     TileChoice tiles;
     int n_ctas = 0, n_items = 0;
     int64_t op_blocks = 0, frame_blocks = 0, b_rows = 0;
@@ -1001,10 +1079,11 @@ srp_status batch_configure(srp_batch_s *b, const TileChoice &t) {
     pa.status = b->d_status;
     // shared memory at launch: at least enough that no more than cps CTAs fit
     // on one SM (so that their TMEM columns always fit, 512 per SM)
-    size_t smem = persist_smem(t, b->split);
+    size_t smem = persist_smem(t, b->split, b->promote);
     smem = std::max(smem, ((size_t)kSmemPerSm / (t.cps + 1) - 1024 + 16 + 15) / 16 * 16);
     const bool conv = b->mode == SRP_MODE_CONV;
     void (*persist)(const CUtensorMap, const PersistArgs) =
+        b->promote ? k_map_batch_tc<true, false, true, true, 2, true> :
         t.cps == 4 ? (conv ? (b->half ? k_map_batch_tc<false, true, true, true, 4>
                                       : k_map_batch_tc<false, false, true, true, 4>)
                            : (b->half ? k_map_batch_tc<false, true, false, true, 4>
@@ -1109,10 +1188,6 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         if (!p->lay.tc)
             return fail(SRP_ERR_UNSUPPORTED,
                         "a batch takes tensor-core plans only (this plan runs on CUDA cores)");
-        if (p->lay.promote > 0)
-            return fail(SRP_ERR_UNSUPPORTED,
-                        "a batch takes no plan whose FP32 accumulators need promotion (a long "
-                        "conventional reduction): map it with srp_map");
     }
     DeviceGuard g(p0->device);
     if (!g.ok) return fail(SRP_ERR_CUDA, "cannot select the plans' device");
@@ -1161,8 +1236,13 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         I.tile_steps = L.tile_steps;
         I.all_streamed = (p->d_w != nullptr && L.tile_steps == L.total_steps) ? 1 : 0;
         if (p->d_w != nullptr) b->any_resident = true;
-        // FP32 split: 3 products per step, all in one accumulator
-        if (p0->precision == SRP_PREC_FP32 && 3.0 * L.mma_steps * kTcAccumBias > kTcBiasLimit)
+        // FP32 split: 3 products per step, all in one accumulator (per epoch
+        // of a promoted plan: at most 4 steps per chunk)
+        I.promote = L.promote;
+        if (L.promote > 0) b->promote = true;
+        const double acc_steps =
+            L.promote > 0 ? std::min<double>(L.mma_steps, 4.0 * L.promote) : (double)L.mma_steps;
+        if (p0->precision == SRP_PREC_FP32 && 3.0 * acc_steps * kTcAccumBias > kTcBiasLimit)
             b->one_acc = false;
         I.max_frames = L.L_max;
         I.pblocks = (L.Q + kPairBlock - 1) / kPairBlock;
@@ -1225,7 +1305,7 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
                     c.stages = st;
                     c.tm = tm != 0;
                     c.mw = mw;
-                    if (tile_fits(c, b->split, b->any_resident, b->one_acc) && best.N == 0)
+                    if (tile_fits(c, b->split, b->any_resident, b->one_acc, b->promote) && best.N == 0)
                         best = c;
                 }
             }
@@ -1287,7 +1367,7 @@ srp_status srp_batch_tune(srp_batch b, const void *const *d_in, const int32_t *L
                 c.cps = cps;
                 c.tm = tm != 0;
                 c.mw = mw;
-                if (!tile_fits(c, b->split, b->any_resident, b->one_acc)) continue;
+                if (!tile_fits(c, b->split, b->any_resident, b->one_acc, b->promote)) continue;
                 if ((result = batch_configure(b, c)) != SRP_OK) break;
                 float ms = 0.0f;
                 for (int rep = 0; rep < 3 && result == SRP_OK; ++rep) {

@@ -511,7 +511,7 @@ srp_status srp_server_create(const srp_handle *plans, int32_t n, const srp_serve
     // and precision (unless batching is off); the rest map on their own
     const srp_plan_s *lead = nullptr;
     for (int i = 0; i < n; ++i)
-        if (plans[i]->lay.tc && plans[i]->lay.promote == 0 && !d->no_batching) {
+        if (plans[i]->lay.tc && !d->no_batching) {
             lead = plans[i];
             break;
         }
@@ -524,7 +524,7 @@ srp_status srp_server_create(const srp_handle *plans, int32_t n, const srp_serve
         si.in_frame_bytes = sizeof(float) * 2 * (size_t)rows * p->lay.Kb;
         si.J = p->lay.J;
         si.max_frames = p->lay.L_max;
-        if (lead != nullptr && p->lay.tc && p->lay.promote == 0 && p->mode == lead->mode &&
+        if (lead != nullptr && p->lay.tc && p->mode == lead->mode &&
             p->precision == lead->precision) {
             si.batch_index = (int)s->batched.size();
             s->batched.push_back(p);

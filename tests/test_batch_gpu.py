@@ -227,22 +227,43 @@ def test_batch_rejects_mixed_modes_and_cuda_core_plans():
     with pytest.raises(srp.SrpError) as e:
         srp.Batch([a, c])
     assert e.value.status == srp.SRP_ERR_UNSUPPORTED
-    # an FP32 conventional plan whose accumulators are promoted maps on its own
-    long = synth.uneven_instance(77, (500, 800), 4, M=16, K=2048)
-    p1 = srp.Plan(long["mic"], long["grid"], long["fs"], long["c"], long["K"],
-                  mode="conventional", max_frames=4)
-    p2 = make_plans(cfgs[1:], "conventional", "fp32", 4)[0]
-    assert p1.info.accum_promotion > 0 and p2.info.accum_promotion == 0
-    with pytest.raises(srp.SrpError) as e:
-        srp.Batch([p2, p1])
-    assert e.value.status == srp.SRP_ERR_UNSUPPORTED
-    p1.close()
-    p2.close()
     batch = srp.Batch([a])
     with pytest.raises(srp.SrpError) as e:  # more frames than the plan takes
         srp.srp_map_batch(batch.handle, [None], [5], None, [None])
     assert e.value.status == srp.SRP_ERR_INVALID_ARG
     batch.close()
+
+
+def test_batch_promoted_conventional_fp32():
+    """FP32 conventional plans with long reductions (M = 16: 120 pairs, K =
+    2048) promote their accumulators every 128 chunks inside the persistent
+    kernel too: a batch of such plans with ordinary ones meets 1e-4 x peak
+    against the oracle, equals each plan's own srp_map to 1e-6 x peak, and
+    keeps doing so when a call skips the promoted plan or maps fewer frames."""
+    long_cfgs = [synth.uneven_instance(77 + i, (500, 900), 4, M=16, K=2048) for i in range(2)]
+    short_cfgs = [synth.uneven_instance(90 + i, (600, 1500), 4, M=M, K=K)
+                  for i, (M, K) in enumerate([(4, 512), (6, 1024)])]
+    cfgs = [long_cfgs[0], short_cfgs[0], long_cfgs[1], short_cfgs[1]]
+    plans = make_plans(cfgs, "conventional", "fp32", 4)
+    assert [p.info.accum_promotion > 0 for p in plans] == [True, False, True, False]
+    assert all(p.info.tensor_cores == 1 for p in plans)
+    batch = srp.Batch(plans)
+    assert batch.info.tiles.operand_a == 1  # the promoting kernel keeps A in TMEM
+    refs = [oracle_maps(c, "conventional", 4) for c in cfgs]
+    for L in ([4, 4, 4, 4], [3, 4, 0, 2]):
+        res = run_batch(batch, cfgs, L)
+        for c, pl, (m, a, p), ref, l in zip(cfgs, plans, res, refs, L):
+            if l == 0:
+                continue
+            check(m, a, p, ref[:l], TOL["fp32"])
+            m1, a1, p1 = pl.map(dev(c["Y"][:l]), L=l)
+            torch.cuda.synchronize()
+            m1 = m1.cpu().numpy()
+            pk = np.abs(m1).max(axis=1)
+            assert np.all(np.abs(m - m1).max(axis=1) <= 1e-6 * pk)
+    batch.close()
+    for pl in plans:
+        pl.close()
 
 
 def test_batch_timing_mode_same_outputs():

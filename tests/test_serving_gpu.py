@@ -188,9 +188,10 @@ def test_deadline_expires_while_queued():
 
 
 def test_unbatched_and_cuda_core_streams():
-    """Streams that are not batched (FP32 conventional plans whose
-    accumulators are promoted, CUDA-core plans, or batching off) map with
-    their own srp_map calls; results equal srp_map."""
+    """CUDA-core plans, and every plan when batching is off, map with their
+    own srp_map calls (results equal srp_map); tensor-core plans, those whose
+    FP32 accumulators are promoted included, go through the batched kernels
+    (results within 1e-6 x peak of srp_map)."""
     cfgs = [synth.uneven_instance(20 + i, (800, 1500), 8, M=M, K=K)
             for i, (M, K) in enumerate([(12, 2048), (4, 512), (9, 1024)])]
     plans = plans_for(cfgs, mode="conventional", precision="fp32", max_frames=8)
@@ -213,7 +214,7 @@ def test_unbatched_and_cuda_core_streams():
             m, a, p = plans[s].map(torch.from_numpy(cfgs[s]["Y"][:8]).cuda())
             torch.cuda.synchronize()
             m = m.cpu().numpy()
-            if batching and plans[s].info.tensor_cores and not plans[s].info.accum_promotion:
+            if batching and plans[s].info.tensor_cores:
                 # the batched kernels
                 pk = np.abs(m).max(axis=1)
                 assert np.all(np.abs(d["maps"] - m).max(axis=1) <= 1e-6 * pk)
