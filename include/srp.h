@@ -235,8 +235,11 @@ SRP_API srp_status srp_map(srp_handle h, const void *d_in, int32_t L, float *d_m
 
 /* srp_map from and to host memory (pinned memory makes the copies
  * asynchronous): copies h_in to the plan's staging buffer, runs srp_map,
- * copies results back and synchronises s before returning.  Needs a plan
- * built with host_io != 0.  h_maps and h_peak may be NULL.                */
+ * copies results back and synchronises s before returning.  Where the GPU
+ * reaches host memory coherently (NVLink-C2C) and h_maps is pinned, the map
+ * kernel stores the maps straight into h_maps instead of a staging buffer
+ * and a copy.  Needs a plan built with host_io != 0.  h_maps and h_peak may
+ * be NULL.                                                                */
 SRP_API srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps,
                         int32_t *h_argmax, float *h_peak, srp_stream_t s);
 

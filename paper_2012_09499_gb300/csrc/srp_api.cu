@@ -727,6 +727,27 @@ srp_status srp_map(srp_handle h, const void *d_in, int32_t L, float *d_maps, int
     return run_map(h, d_in, L, d_maps, d_argmax, d_peak, reinterpret_cast<cudaStream_t>(s));
 }
 
+// Device address of a pinned (page-locked or registered) host buffer on a
+// GPU that reaches host memory coherently (NVLink-C2C, host page tables), or
+// null: the map kernel then stores the maps straight into the caller's buffer
+// instead of into a device staging buffer followed by a copy.
+static float *direct_host_maps(int device, float *h_maps) {
+    if (h_maps == nullptr) return nullptr;
+    int coherent = 0;
+    if (cudaDeviceGetAttribute(&coherent, cudaDevAttrPageableMemoryAccessUsesHostPageTables,
+                               device) != cudaSuccess || !coherent) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, h_maps) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+    return static_cast<float *>(at.devicePointer);
+}
+
 srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps,
                         int32_t *h_argmax, float *h_peak, srp_stream_t s) {
     srp_status st = check_handle(h);
@@ -744,10 +765,11 @@ srp_status srp_map_host(srp_handle h, const void *h_in, int32_t L, float *h_maps
     const size_t in_bytes = sizeof(float2) * (size_t)L * rows * lay.Kb;
     SRP_CUDA(cudaMemcpyAsync(h->d_in_stage, h_in, in_bytes, cudaMemcpyHostToDevice, cs),
              "copy input to device");
-    st = run_map(h, h->d_in_stage, L, h_maps ? h->d_maps_stage : nullptr, h->d_argmax_stage,
-                 h->d_peak_stage, cs);  // slot 0
+    float *direct = direct_host_maps(h->device, h_maps);
+    st = run_map(h, h->d_in_stage, L, h_maps ? (direct ? direct : h->d_maps_stage) : nullptr,
+                 h->d_argmax_stage, h->d_peak_stage, cs);  // slot 0
     if (st != SRP_OK) return st;
-    if (h_maps)
+    if (h_maps && !direct)
         SRP_CUDA(cudaMemcpyAsync(h_maps, h->d_maps_stage, sizeof(float) * (size_t)L * lay.J,
                                  cudaMemcpyDeviceToHost, cs), "copy maps to host");
     SRP_CUDA(cudaMemcpyAsync(h_argmax, h->d_argmax_stage, sizeof(int32_t) * L,
@@ -807,6 +829,9 @@ srp_status srp_map_host_async(srp_handle h, const void *h_in, int32_t L, float *
     // map: once the input is in and the slot's previous results have left
     SRP_CUDA(cudaStreamWaitEvent(cs, h->ev_in[k], 0), "order map");
     SRP_CUDA(cudaStreamWaitEvent(cs, h->ev_out[k], 0), "order map");
+    // (the maps go through the staging slot and a copy even into pinned
+    // buffers: stores from the map kernel to host memory would hold the next
+    // step's map back, while the copy overlaps it)
     st = run_map(h, sp.in, L, h_maps ? sp.maps : nullptr, sp.argmax, sp.peak, cs);
     if (st != SRP_OK) return st;
     SRP_CUDA(cudaEventRecord(h->ev_done[k], cs), "record map");

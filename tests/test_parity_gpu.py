@@ -462,6 +462,35 @@ def test_long_conventional_reduction_fp32():
             check_rescored_argmax(idx, peak, ref)
 
 
+def test_host_entry_into_pinned_buffers_equals_device_map():
+    """srp_map_host with page-locked result buffers (where the GPU reaches host
+    memory coherently, the map kernel stores the maps straight into them)
+    gives exactly the maps, argmax and peak of srp_map, and so does a
+    pageable result buffer (staging and copy); twice in a row."""
+    cfg = synth.tiny_2d(seed=23, L=12)
+    plan = srp.Plan(cfg["mic"], cfg["grid"], cfg["fs"], cfg["c"], cfg["K"], max_frames=12,
+                    host_io=1)
+    J = cfg["grid"].shape[0]
+    m0, a0, p0 = plan.map(dev(cfg["Y"]))
+    torch.cuda.synchronize()
+    m0, a0, p0 = m0.cpu().numpy(), a0.cpu().numpy(), p0.cpu().numpy()
+    h_in = torch.from_numpy(np.ascontiguousarray(cfg["Y"])).pin_memory()
+    for pinned in (True, False, True):
+        if pinned:
+            hm = torch.full((12, J), np.nan, dtype=torch.float32).pin_memory()
+            ha = torch.zeros(12, dtype=torch.int32).pin_memory()
+            hp = torch.zeros(12, dtype=torch.float32).pin_memory()
+            srp.srp_map_host(plan.handle, h_in, 12, hm, ha, hp)
+            hm, ha, hp = hm.numpy(), ha.numpy(), hp.numpy()
+        else:
+            hm = np.full((12, J), np.nan, np.float32)
+            ha = np.zeros(12, np.int32)
+            hp = np.zeros(12, np.float32)
+            srp.srp_map_host(plan.handle, cfg["Y"], 12, hm, ha, hp)
+        assert np.array_equal(hm, m0) and np.array_equal(ha, a0) and np.array_equal(hp, p0)
+    plan.close()
+
+
 def test_host_async_pipeline_matches_host_entry():
     """srp_map_host_async over consecutive steps (two staging slots, copies
     overlapped with the neighbouring maps) gives exactly srp_map_host's
