@@ -496,7 +496,7 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
                                 lay.J_pad, lay.Q, h->d_xs, lay.xf, h->d_nq, h->d_off, lay.n_aux,
                                 h->d_xi32, lay.S_pad, psi_fp32, lay.K, L, kRescoreDelta,
                                 h->d_rs_fkey, h->d_rs_slots, h->d_rs_count, d_argmax, d_peak,
-                                s),
+                                d_maps, s),
                  "argmax re-scoring kernel");
     } else {
         // tensor-core tiles raise one key per frame (d_part[0, L)); CUDA-core

@@ -37,6 +37,7 @@
 
 #include "srp_device.cuh"
 #include "srp_internal.h"
+#include "srp_rescore.cuh"
 #include "srp_tc_common.cuh"
 
 namespace srp {
@@ -70,6 +71,10 @@ struct BatchInst {
     int promote;              // FP32 conventional: chunks per accumulator epoch (0: one epoch)
     int64_t op_row0;          // first block of the plan in the operand kernel's grid
     int64_t frame0;           // first block of the plan in the argmax kernel's grid
+    // FP32 re-scoring of the maximiser (BF16 / FP16 Nyquist plans that ask for it)
+    const int32_t *off;       // [Q] first slot of pair q among the S unpadded samples
+    float *x32;               // [max_frames][S32] FP32 samples written by the operand kernel, or null
+    int S32;
 };
 
 // Per-call arguments of one plan (device table, rewritten by every call).
@@ -212,6 +217,7 @@ __global__ void __launch_bounds__(kOpThreads) k_batch_operands(const BatchInst *
     __syncthreads();
     gcc_rows(tw, ps, Kb, np, K, [&](int j) { return I.nq[q0 + j] + I.n_aux; },
              [&](int j, int t, int nl, float v) {
+                 if (I.x32 != nullptr) I.x32[(size_t)l * I.S32 + I.off[q0 + j] + t] = v;
                  if (nl & 1) v = -v;
                  const int s = I.offc[q0 + j] + t;
                  const uint16_t h = to16(v, kFmt == 2);
@@ -250,6 +256,105 @@ __global__ void __launch_bounds__(256) k_batch_argmax(const BatchInst *__restric
             call[p].argmax[l] = (int32_t)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull));
             if (call[p].peak != nullptr) call[p].peak[l] = key_value(k);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Argmax with FP32 re-scoring: one CTA of kBrsThreads per (plan, frame).  For
+// a plan with FP32 samples (x32), the tiles whose reduced-precision maximum
+// is at least m - kRescoreDelta |m| (m the frame's maximum) are evaluated
+// again candidate by candidate in FP32 (Eq. SRPapprox, rs::nyquist_at: four
+// threads per candidate over quarters of the pairs, added in a fixed order),
+// as srp_map does for such a plan; the lowest-index maximiser of those values
+// is the frame's argmax and its FP32 value the peak.  Other plans, and frames
+// with more than kRescoreMaxTiles such tiles (a nearly flat map), keep the
+// reduced-precision maximiser.
+// ---------------------------------------------------------------------------
+constexpr int kBrsParts = 4, kBrsThreads = kBrsParts * kTileJ, kBrsWarps = kBrsThreads / 32;
+constexpr int kBrsSmemFloats = 12 * 1024;  // a frame's FP32 samples staged in shared memory (48 KB)
+constexpr int kBrsCandCap = 2048;          // candidates scored one by one (else whole tiles)
+static_assert(kBrsThreads >= kRescoreMaxTiles, "one thread per selected tile when sorting");
+
+__device__ __forceinline__ unsigned long long block_max_brs(unsigned long long k,
+                                                            unsigned long long *red) {
+    k = warp_max_u64(k);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = k;
+    __syncthreads();
+    k = 0ull;
+#pragma unroll
+    for (int w = 0; w < kBrsWarps; ++w) k = red[w] > k ? red[w] : k;
+    __syncthreads();
+    return k;
+}
+
+__global__ void __launch_bounds__(kBrsThreads) k_batch_rescore(const BatchInst *__restrict__ inst,
+                                                                const BatchCall *__restrict__ call,
+                                                                int n) {
+    __shared__ unsigned long long red[kBrsWarps];
+    __shared__ int tiles[kRescoreMaxTiles];
+    __shared__ int n_sel, n_cand;
+    __shared__ int cand[kBrsCandCap];
+    __shared__ float part_sum[kBrsParts * kTileJ];
+    extern __shared__ float xi_sm[];
+    const int64_t blk = blockIdx.x;
+    const int p = find_plan(n, blk, [&](int i) { return inst[i].frame0; });
+    const BatchInst &I = inst[p];
+    const int l = (int)(blk - I.frame0);
+    if (l >= call[p].L) return;
+    const unsigned long long *part = I.part + (size_t)l * I.n_tiles;
+    unsigned long long k = 0ull;
+    for (int t = threadIdx.x; t < I.n_tiles; t += blockDim.x) {
+        const unsigned long long v = part[t];
+        k = v > k ? v : k;
+    }
+    const unsigned long long kmax = block_max_brs(k, red);
+    const float m = key_value(kmax);
+    unsigned long long best = kmax;
+    if (I.x32 != nullptr) {
+        if (threadIdx.x == 0) n_sel = 0;
+        __syncthreads();
+        const uint32_t otau = ordered_value(m - kRescoreDelta * fabsf(m));
+        for (int t = threadIdx.x; t < I.n_tiles; t += blockDim.x)
+            if ((uint32_t)(part[t] >> 32) >= otau) {
+                const int slot = atomicAdd(&n_sel, 1);
+                if (slot < kRescoreMaxTiles) tiles[slot] = t;
+            }
+        __syncthreads();
+        const int ns = n_sel;
+        if (ns <= kRescoreMaxTiles) {
+            // ascending tile order (the atomics fill the list in any order)
+            int tt = 0, rank = 0;
+            if (threadIdx.x < ns) {
+                tt = tiles[threadIdx.x];
+                for (int j = 0; j < ns; ++j) rank += tiles[j] < tt ? 1 : 0;
+            }
+            __syncthreads();
+            if (threadIdx.x < ns) tiles[rank] = tt;
+            __syncthreads();
+            // the frame's FP32 samples, in shared memory when they fit
+            const float *xr = I.x32 + (size_t)l * I.S32;
+            if (I.S32 <= kBrsSmemFloats) {
+                for (int t = threadIdx.x; t < I.S32; t += blockDim.x) xi_sm[t] = xr[t];
+                __syncthreads();
+                xr = xi_sm;
+            }
+            // the candidates that reach the threshold in the map when it is
+            // written, else every candidate of the tiles
+            const float *maps_row =
+                call[p].maps != nullptr ? call[p].maps + (size_t)l * I.J : nullptr;
+            unsigned long long b = rs::score_candidates<kBrsParts>(
+                tiles, 0, 1, ns, maps_row, otau, I.J, cand, kBrsCandCap, &n_cand, part_sum,
+                [&](int64_t i, int q) {
+                    return rs::nyquist_at(I.xs, I.J_pad, i, I.Q, I.xf, I.nq, I.off, I.n_aux, xr,
+                                          q, kBrsParts);
+                });
+            b = block_max_brs(b, red);
+            if (b != 0ull) best = b;
+        }
+    }
+    if (threadIdx.x == 0) {
+        call[p].argmax[l] = (int32_t)(0xFFFFFFFFu - (uint32_t)(best & 0xFFFFFFFFull));
+        if (call[p].peak != nullptr) call[p].peak[l] = key_value(best);
     }
 }
 
@@ -905,6 +1010,8 @@ struct srp_batch_s {
     size_t b_cap = 0;
     unsigned long long *d_part = nullptr;
     size_t part_bytes = 0;
+    float *d_x32 = nullptr;     // FP32 samples of the plans whose maximiser is re-scored
+    bool rescore = false;       // some plan re-scores its maximiser (the argmax kernel does)
     int *d_status = nullptr;
     alignas(64) unsigned char b_map[128] = {};
     // the three kernels of a call, as captured in the graph
@@ -939,6 +1046,7 @@ void batch_release(srp_batch_s *b) {
     cudaFree(b->d_cta_first);
     cudaFree(b->d_b);
     cudaFree(b->d_part);
+    cudaFree(b->d_x32);
     cudaFree(b->d_status);
 }
 
@@ -964,7 +1072,11 @@ cudaError_t enqueue_kernels(srp_batch_s *b, cudaStream_t s, bool timed) {
     if (timed) cudaEventRecord(b->ev[1], s);
     b->persist<<<(unsigned)b->n_ctas, kThreads, b->persist_smem_bytes, s>>>(map, b->pargs);
     if (timed) cudaEventRecord(b->ev[2], s);
-    k_batch_argmax<<<(unsigned)b->frame_blocks, 256, 0, s>>>(b->d_inst, b->d_call, n);
+    if (b->rescore)
+        k_batch_rescore<<<(unsigned)b->frame_blocks, kBrsThreads, kBrsSmemFloats * sizeof(float),
+                          s>>>(b->d_inst, b->d_call, n);
+    else
+        k_batch_argmax<<<(unsigned)b->frame_blocks, 256, 0, s>>>(b->d_inst, b->d_call, n);
     if (timed) cudaEventRecord(b->ev[3], s);
     return cudaGetLastError();
 }
@@ -1206,7 +1318,7 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
     b->plans.assign(plans, plans + n);
     cudaError_t e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
-    size_t part = 0;
+    size_t part = 0, x32 = 0;
     b->inst.resize(n);
     for (int i = 0; i < n; ++i) {
         const srp_plan_s *p = plans[i];
@@ -1246,6 +1358,12 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
             b->one_acc = false;
         I.max_frames = L.L_max;
         I.pblocks = (L.Q + kPairBlock - 1) / kPairBlock;
+        I.off = p->d_off;
+        I.S32 = L.S;
+        if (L.rescore && p0->mode == SRP_MODE_NYQUIST) {
+            b->rescore = true;
+            x32 += sizeof(float) * (size_t)L.L_max * L.S;
+        }
         part += sizeof(unsigned long long) * (size_t)L.L_max * L.n_tiles;
         b->max_L = std::max(b->max_L, L.L_max);
         b->max_K = std::max(b->max_K, L.K);
@@ -1254,6 +1372,19 @@ srp_status srp_batch_create(const srp_handle *plans, int32_t n, const srp_batch_
         return bail(fail(SRP_ERR_UNSUPPORTED, "K too large for the batched operand kernel"));
     if ((e = cudaMalloc(&b->d_part, part)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     b->part_bytes = part;
+    if (x32 > 0) {
+        if ((e = cudaMalloc(&b->d_x32, x32)) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMalloc"));
+        size_t off = 0;
+        for (int i = 0; i < n; ++i) {
+            if (!(plans[i]->lay.rescore && p0->mode == SRP_MODE_NYQUIST)) continue;
+            b->inst[i].x32 = b->d_x32 + off / sizeof(float);
+            off += sizeof(float) * (size_t)b->inst[i].max_frames * b->inst[i].S32;
+        }
+        if ((e = cudaFuncSetAttribute(k_batch_rescore, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kBrsSmemFloats * sizeof(float)))) != cudaSuccess)
+            return bail(cuda_fail(e, "re-scoring kernel attribute"));
+    }
     {
         size_t off = 0;
         for (int i = 0; i < n; ++i) {

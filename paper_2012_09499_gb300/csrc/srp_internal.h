@@ -213,7 +213,7 @@ cudaError_t launch_rescore(bool conv, const unsigned long long *part, int n_tile
                            const int32_t *off, int n_aux, const float *xi32, int S32,
                            const float2 *psi, int K, int L, float delta,
                            const unsigned long long *fkey, unsigned long long *slots, int *count,
-                           int32_t *argmax, float *peak, cudaStream_t s);
+                           int32_t *argmax, float *peak, const float *maps, cudaStream_t s);
 cudaError_t launch_argmax(const unsigned long long *part, int n_tiles, int L, int32_t *argmax,
                           float *peak, cudaStream_t s);
 

@@ -32,67 +32,26 @@
 
 #include "srp_device.cuh"
 #include "srp_internal.h"
+#include "srp_rescore.cuh"
 
 namespace srp {
 namespace {
 
 using namespace dev;
+using rs::nyquist_at;
 
 constexpr int kRsParts = 4;                   // Nyquist: threads per candidate
 constexpr int kRsThreads = kRsParts * kTileJ;  // Nyquist: one tile per CTA and pass
 constexpr int kRsWarps = kRsThreads / 32;
 static_assert(kRsThreads >= kRescoreMaxTiles, "one thread per selected tile when sorting");
-constexpr float kExactF = 9.094947017729282e-13f;  // 2^-40: f of an exact sample, as in the plan
 constexpr int kRsSmemFloats = 12 * 1024;  // a frame's FP32 samples staged in shared memory (48 KB)
+constexpr int kRsCandCap = 2048;          // candidates scored one by one (else whole tiles)
 
 // Sum over the warp in a fixed order (the same butterfly every time).
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     return v;
-}
-
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// Eq. SRPapprox summed over the pairs q_first, q_first + q_step, ... at
-// candidate i, by one thread (the threads of a warp take consecutive
-// candidates, so the table reads are coalesced), for one frame's FP32 samples xi (pair q's 2 nmax + 1 samples
-// from off[q], lag n at n + nmax; every thread reads the same sample at the
-// same time): with x = x0 + f, sinc(x - n) = (-1)^n sp / (f + x0 - n), sp =
-// (-1)^x0 sin(pi f) / pi from the plan's table.  f + (x0 - n) is rounded
-// once (x0 - n is an exact integer) and its reciprocal is the hardware
-// approximation (within an ulp), as in the tensor-core generator.
-__device__ float nyquist_at(const int2 *__restrict__ xs, int64_t J_pad, int64_t i, int Q, int xf,
-                            const int32_t *__restrict__ nq, const int32_t *__restrict__ off,
-                            int n_aux, const float *xi, int q_first, int q_step) {
-    float acc = 0.0f;
-    int2 nxt = q_first < Q ? __ldg(&xs[(size_t)q_first * J_pad + i]) : make_int2(0, 0);
-    for (int q = q_first; q < Q; q += q_step) {
-        const int2 e = nxt;
-        if (q + q_step < Q) nxt = __ldg(&xs[(size_t)(q + q_step) * J_pad + i]);
-        int x0;
-        float f;
-        decode_tdoa(e.x, xf, x0, f);
-        if (f == 0.0f) f = kExactF;
-        const float sp = __int_as_float(e.y);
-        const int nmax = __ldg(&nq[q]) + n_aux;
-        const float *r = xi + __ldg(&off[q]);
-        const int base = x0 + nmax;  // f + base - t = f + x0 - n for slot t = n + nmax
-        const float sg = (nmax & 1) ? -sp : sp;  // (-1)^n sp at n = -nmax
-        float s0 = 0.0f, s1 = 0.0f;  // even and odd slots
-        int t = 0;
-        for (; t + 1 <= 2 * nmax; t += 2) {
-            s0 = fmaf(rcp_approx(f + (float)(base - t)), r[t], s0);
-            s1 = fmaf(rcp_approx(f + (float)(base - t - 1)), r[t + 1], s1);
-        }
-        s0 = fmaf(rcp_approx(f + (float)(base - t)), r[t], s0);  // the last slot, t = 2 nmax
-        acc = fmaf(sg, s0 - s1, acc);
-    }
-    return acc;
 }
 
 // The conventional map at candidate i, by one warp, for one frame's cross
@@ -168,10 +127,11 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(
     const int32_t *__restrict__ off, int n_aux, const float *__restrict__ xi32, int S32,
     const float2 *__restrict__ psi, int K, float delta, const unsigned long long *fkey,
     unsigned long long *slots, int *count, int32_t *__restrict__ argmax,
-    float *__restrict__ peak) {
+    float *__restrict__ peak, const float *__restrict__ maps) {
     __shared__ unsigned long long red[kRsWarps];
     __shared__ int tiles[kRescoreMaxTiles];
-    __shared__ int n_sel, last;
+    __shared__ int n_sel, last, n_cand;
+    __shared__ int cand[kRsCandCap];
     const int l = blockIdx.x, g = blockIdx.y, G = gridDim.y;
     // launched behind the map kernel with programmatic stream serialization:
     // wait until its tile keys are complete and visible
@@ -248,25 +208,14 @@ __global__ void __launch_bounds__(kRsThreads) k_rescore(
             }
         }
     } else {
-        // selected tile j goes to CTA j mod G; candidate r of the tile to the
-        // kRsParts threads r + kTileJ p, thread p summing the pairs q = p mod
-        // kRsParts; the parts are then added in the order p = 0, 1, ...
-        __shared__ float part_sum[kRsParts][kTileJ];
-        const int r = threadIdx.x % kTileJ, p = threadIdx.x / kTileJ;
-        for (int j = g; j < ns; j += G) {
-            const int64_t i = (int64_t)tiles[j] * kTileJ + r;
-            if (i < J)
-                part_sum[p][r] = nyquist_at(xs, J_pad, i, Q, xf, nq, off, n_aux, xr, p, kRsParts);
-            __syncthreads();
-            if (p == 0 && i < J) {
-                float v = part_sum[0][r];
-#pragma unroll
-                for (int u = 1; u < kRsParts; ++u) v += part_sum[u][r];
-                const unsigned long long key = argmax_key(v, (uint32_t)i);
-                best = key > best ? key : best;
-            }
-            __syncthreads();
-        }
+        // selected tile j goes to CTA j mod G (its candidates that reach the
+        // threshold in the map, when the map is written)
+        __shared__ float part_sum[kRsParts * kTileJ];
+        best = rs::score_candidates<kRsParts>(
+            tiles, g, G, ns, maps != nullptr ? maps + (size_t)l * J : nullptr, otau, J, cand,
+            kRsCandCap, &n_cand, part_sum, [&](int64_t i, int p) {
+                return nyquist_at(xs, J_pad, i, Q, xf, nq, off, n_aux, xr, p, kRsParts);
+            });
     }
     best = block_max(best, red);
     // this CTA's best key; the frame's last CTA to arrive reduces them all
@@ -298,8 +247,16 @@ cudaError_t launch_rescore(bool conv, const unsigned long long *part, int n_tile
                            const int32_t *off, int n_aux, const float *xi32, int S32,
                            const float2 *psi, int K, int L, float delta,
                            const unsigned long long *fkey, unsigned long long *slots, int *count,
-                           int32_t *argmax, float *peak, cudaStream_t s) {
+                           int32_t *argmax, float *peak, const float *maps, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {  // up to 48 KB of staged samples beside the static arrays
+        cudaError_t e = cudaFuncSetAttribute(k_rescore<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(float) * kRsSmemFloats));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     cudaLaunchConfig_t cfg = {};
     // the conventional map scores a warp per candidate, the Nyquist map a CTA
     // per tile: all kRescoreCtas CTAs per frame, or a quarter of them
@@ -314,10 +271,10 @@ cudaError_t launch_rescore(bool conv, const unsigned long long *part, int n_tile
     cfg.numAttrs = 1;
     cudaError_t e = conv ? cudaLaunchKernelEx(&cfg, k_rescore<true>, part, n_tiles, J, J_pad, Q, xs,
                                               xf, nq, off, n_aux, xi32, S32, psi, K, delta, fkey,
-                                              slots, count, argmax, peak)
+                                              slots, count, argmax, peak, maps)
                          : cudaLaunchKernelEx(&cfg, k_rescore<false>, part, n_tiles, J, J_pad, Q,
                                               xs, xf, nq, off, n_aux, xi32, S32, psi, K, delta,
-                                              fkey, slots, count, argmax, peak);
+                                              fkey, slots, count, argmax, peak, maps);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -24,6 +24,18 @@ def mix(seed, n, J_range, L, **fix):
     return [synth.uneven_instance(seed * 1000 + i, J_range, L, **fix) for i in range(n)]
 
 
+def check_fp32_maximiser(idx, peak, ref):
+    """BF16 / FP16 plans choose the maximiser in FP32: the oracle's first
+    maximiser except on FP32 ties (gap below 1e-4 x peak), the peak its FP32
+    value within 1e-4 x peak."""
+    pk = np.abs(ref).max(axis=1)
+    rows = np.arange(ref.shape[0])
+    assert np.all(np.abs(peak.astype(np.float64) - ref[rows, idx]) <= 1e-4 * pk)
+    ridx = np.argmax(ref, axis=1)
+    for l in np.nonzero(idx != ridx)[0]:
+        assert ref[l, ridx[l]] - ref[l, idx[l]] < 1e-4 * pk[l]
+
+
 def plans_for(cfgs, mode="nyquist", precision="bf16", max_frames=32):
     return [srp.Plan(c["mic"], c["grid"], c["fs"], c["c"], c["K"], mode=mode, n_aux=2,
                      precision=precision, max_frames=max_frames) for c in cfgs]
@@ -65,11 +77,12 @@ def test_result_alone_equals_result_in_the_mix():
     assert np.array_equal(again["maps"], a0["maps"])
     assert np.array_equal(again["argmax"], a0["argmax"])
     assert np.array_equal(again["peak"], a0["peak"])
-    # every map that came back is within the BF16 tolerance of the oracle
+    # every map that came back is within the BF16 tolerance of the oracle, and
+    # the maximiser, chosen in FP32, is the oracle's (up to FP32 ties)
     ref = oracle_maps(cfgs[2], probe)
     pk = np.abs(ref).max(axis=1)
     assert np.all(np.abs(a0["maps"] - ref).max(axis=1) <= 1e-2 * pk)
-    assert np.array_equal(a0["argmax"], np.argmax(a0["maps"], axis=1))
+    check_fp32_maximiser(a0["argmax"], a0["peak"], ref)
     for d in done:
         if d["maps"] is None or d["tag"] < 100:
             continue
@@ -77,7 +90,7 @@ def test_result_alone_equals_result_in_the_mix():
         ref = oracle_maps(cfgs[s], cfgs[s]["Y"][f0:f0 + 8])
         pk = np.abs(ref).max(axis=1)
         assert np.all(np.abs(d["maps"] - ref).max(axis=1) <= 1e-2 * pk)
-        assert np.array_equal(d["argmax"], np.argmax(d["maps"], axis=1))
+        check_fp32_maximiser(d["argmax"], d["peak"], ref)
     # latencies are ordered and positive
     for d in done:
         assert d["t_submit"] <= d["t_start"] <= d["t_done"]
