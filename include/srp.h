@@ -390,7 +390,10 @@ SRP_API srp_status srp_refiner_destroy(srp_refiner r);
  * a work list of (plan, 128-candidate tile, frame tile) items, spread over
  * the SMs longest-first onto the least-loaded CTA; and the per-frame argmax
  * of every plan.  Each plan's maps, argmax and peak are exactly what srp_map
- * defines, up to floating-point rounding.
+ * defines, up to floating-point rounding; BF16/FP16 Nyquist plans that re-score
+ * their maximiser (srp_plan_info.argmax_rescored) re-score it in the batch
+ * too, while conventional BF16/FP16 plans keep their map's own maximiser in a
+ * batch.
  *
  * The batch reads the plans' device tables in place (the plans must outlive
  * the batch and must not be destroyed while it is in use) and owns its own
