@@ -108,6 +108,15 @@ def test_rescored_batch_argmax_equals_per_plan_map(precision):
             a1, p1 = a1.cpu().numpy()[:l], p1.cpu().numpy()[:l]
             assert np.all(np.abs(p - p1) <= 1e-6 * np.abs(p1))
             assert np.mean(a == a1) >= 0.9  # any other frame is an FP32 near-tie (peaks above)
+    # without maps the whole selected tiles are scored: the same maximisers
+    L = [16, 16, 16, 16]
+    full = run_batch(batch, cfgs, L)
+    d_in = [dev(c["Y"][:l]) for c, l in zip(cfgs, L)]
+    bare = batch.map(d_in, L=L, maps=False)
+    torch.cuda.synchronize()
+    for (m, a, p), (m2, a2, p2) in zip(full, bare):
+        assert m2 is None
+        assert np.array_equal(a, a2.cpu().numpy()) and np.array_equal(p, p2.cpu().numpy())
     batch.close()
     for pl in plans:
         pl.close()
