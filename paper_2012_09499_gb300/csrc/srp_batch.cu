@@ -562,17 +562,20 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_map_batch_tc(const __grid_co
                     int bk = -1;
                     const float *row_p = mt + fr * kMtStride;
                     if (kmax == 128) {  // full tile: 64 candidates per thread, unrolled
+                        // (FP32 compares: the same first maximiser as the ordered
+                        // values for finite maps, -0 equal to +0)
                         const float *rp = row_p + h;
                         int bj = 0;
-                        bo = ordered_value(rp[0]);
+                        float bv = rp[0];
 #pragma unroll
                         for (int j = 1; j < 64; ++j) {
-                            const uint32_t o = ordered_value(rp[2 * j]);
-                            if (o > bo) {
-                                bo = o;
+                            const float v = rp[2 * j];
+                            if (v > bv) {
+                                bv = v;
                                 bj = j;
                             }
                         }
+                        bo = ordered_value(bv);
                         bk = h + 2 * bj;
                     } else {
                         for (int k = h; k < kmax; k += 2) {

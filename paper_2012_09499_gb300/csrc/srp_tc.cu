@@ -194,6 +194,8 @@ struct TcArgs {
     int n_tiles;
     int *status;
     int vec_maps;           // maps rows are 8-byte aligned (float2 stores)
+    int bulk_maps;          // maps in device memory, 16-byte aligned, J % 4 == 0: one
+                            // bulk store per frame row of a tile
     uint32_t a_col0;        // operand A in TMEM: first column of the A stages
     int par1_used;          // the tile has two or more 16-lag steps: accumulator 1 is written
     const uint4 *w;         // resident operand A (kW): the plan's interpolation matrix
@@ -501,10 +503,19 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
             for (int jj = 0; jj < 16; ++jj) mt[(j0 + jj) * kMtStride + r] = v[jj];
         }
         tc_fence_before();
+        if (a.bulk_maps) fence_proxy_async();  // mt's stores before the bulk copies read it
         asm volatile("bar.sync 1, 128;" ::: "memory");
         const int64_t tile0 = (int64_t)blockIdx.x * 128;
         const int n_rows = min(a.N, a.L - l0);
-        if (a.maps != nullptr) {  // warp w writes frame rows w, w + 4, ...
+        if (a.bulk_maps) {  // warp w's lane 0 copies frame rows w, w + 4, ... out
+            if (lane == 0) {
+                const uint32_t bytes = 4u * (uint32_t)min((int64_t)128, a.J - tile0);
+                for (int fr = warp; fr < n_rows; fr += 4)
+                    bulk_store(a.maps + (size_t)(l0 + fr) * a.J + tile0,
+                               smem_u32(mt + fr * kMtStride), bytes);
+                bulk_commit();
+            }
+        } else if (a.maps != nullptr) {  // warp w writes frame rows w, w + 4, ...
             for (int fr = warp; fr < n_rows; fr += 4) {
                 float *dst = a.maps + (size_t)(l0 + fr) * a.J + tile0;
                 const float *srcr = mt + fr * kMtStride;
@@ -531,17 +542,20 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
                 const float *row_p = mt + fr * kMtStride;
                 const int kmax = (int)min((int64_t)128, a.J - tile0);
                 if (kmax == 128) {  // full tile: 64 candidates per thread, unrolled
+                    // (FP32 compares: the same first maximiser as the ordered
+                    // values for finite maps, -0 equal to +0)
                     const float *rp = row_p + h;
                     int bj = 0;
-                    bo = ordered_value(rp[0]);
+                    float bv = rp[0];
 #pragma unroll
                     for (int j = 1; j < 64; ++j) {
-                        const uint32_t o = ordered_value(rp[2 * j]);
-                        if (o > bo) {
-                            bo = o;
+                        const float v = rp[2 * j];
+                        if (v > bv) {
+                            bv = v;
                             bj = j;
                         }
                     }
+                    bo = ordered_value(bv);
                     bk = h + 2 * bj;
                 } else {
                     for (int k = h; k < kmax; k += 2) {
@@ -567,6 +581,7 @@ __global__ void __launch_bounds__(kThreads, kOcc) k_interp_tc(const __grid_const
                 }
             }
         }
+        if (a.bulk_maps && lane == 0) bulk_wait_read();
     } else if (warp == kTmaWarp) {
         // ---------------- B loads (GCC samples) ----------------
         if (lane == 0) {
@@ -953,6 +968,15 @@ cudaError_t launch_interp_tc(const void *xi_map, int N, const int2 *xs, const in
     a.par1_used = a.mma_warps == 2 ? par1_used : 0;
     a.K = K;
     a.vec_maps = (maps != nullptr && (J % 2) == 0 && (reinterpret_cast<uintptr_t>(maps) & 7) == 0);
+    a.bulk_maps = 0;
+    if (maps != nullptr && (J % 4) == 0 && (reinterpret_cast<uintptr_t>(maps) & 15) == 0) {
+        // maps written straight into host memory keep the per-thread stores
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, maps) == cudaSuccess &&
+            pa.type == cudaMemoryTypeDevice)
+            a.bulk_maps = 1;
+        (void)cudaGetLastError();
+    }
     a.w = static_cast<const uint4 *>(w);
     a.woff = woff;
     a.tile_steps = tile_steps;

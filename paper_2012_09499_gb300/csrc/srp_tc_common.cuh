@@ -23,7 +23,8 @@ constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
 constexpr int kXRing = 8;            // (TDOA, sp) prefetch ring (slots per candidate row)
 constexpr int kXAhead = kXRing - 1;  // pairs in flight ahead of the current one
 constexpr int kXRingW = 4;           // the same ring in the kernel that also streams A blocks
-constexpr int kMtStride = 130;       // floats per frame row of the epilogue tile
+constexpr int kMtStride = 132;       // floats per frame row of the epilogue tile (rows
+                                     // 16-byte aligned for bulk stores)
 constexpr int kMaxStages = 4;        // pipeline stages the kernels' barrier blocks hold
 
 // ---------------------------------------------------------------------------
@@ -176,6 +177,43 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b,
                  : "memory");
 }
 
+// 8, 16 or 32 consecutive 32-bit TMEM columns of this thread's lane in one
+// instruction (v[0] at column taddr).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {"
+        "%1, %2, %3, %4, %5, %6, %7, %8};"
+        ::"r"(taddr),
+          "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {"
+        "%1, %2, %3, %4, %5, %6, %7, %8, "
+        "%9, %10, %11, %12, %13, %14, %15, %16};"
+        ::"r"(taddr),
+          "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+          "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {"
+        "%1, %2, %3, %4, %5, %6, %7, %8, "
+        "%9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, "
+        "%25, %26, %27, %28, %29, %30, %31, %32};"
+        ::"r"(taddr),
+          "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+          "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+          "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+          "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -224,6 +262,23 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
             dst),
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
+}
+
+// Bulk copy of bytes (a multiple of 16, both addresses 16-byte aligned) from
+// shared to global memory, in this thread's bulk group.  The shared source
+// may be reused once bulk_wait_read() has returned.
+__device__ __forceinline__ void bulk_store(void *dst, uint32_t src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(src), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
@@ -331,6 +386,41 @@ __device__ __forceinline__ void store_group(uint32_t dst0, uint32_t dst1, uint32
     }
 }
 
+// Store the NG groups cc0 .. cc0 + NG - 1 of a candidate row (hv[cc][e], and
+// lv with kSplit).  In tensor memory the row's 4 NG columns are consecutive,
+// so they go out as one x32 store (NG = 8), x16 + x8 (NG = 6), x16 or x8
+// instead of NG x4 stores.
+template <int NG, bool kSplit, int kDst>
+__device__ __forceinline__ void store_row(uint32_t dst0, uint32_t dst1, uint32_t sw,
+                                          uint32_t cc0, const uint32_t (&hv)[NG][4],
+                                          const uint32_t (&lv)[NG][4], uint4 *g0, uint4 *g1) {
+    if (kDst == kATmem) {
+#pragma unroll
+        for (int part = 0; part < (kSplit ? 2 : 1); ++part) {
+            const uint32_t *v = part ? &lv[0][0] : &hv[0][0];
+            const uint32_t t = (part ? dst1 : dst0) + 4u * cc0;
+            if (NG == 8) {
+                tmem_st32(t, v);
+            } else if (NG == 6) {
+                tmem_st16(t, v);
+                tmem_st8(t + 16u, v + 16);
+            } else if (NG == 4) {
+                tmem_st16(t, v);
+            } else if (NG == 2) {
+                tmem_st8(t, v);
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < NG; ++cc)
+                    tmem_st4(t + 4u * cc, v[4 * cc], v[4 * cc + 1], v[4 * cc + 2], v[4 * cc + 3]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int cc = 0; cc < NG; ++cc)
+            store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv[cc], lv[cc], g0, g1);
+    }
+}
+
 // Weights of NG groups of 8 lags for one candidate row of operand A:
 // w = sp / d with d = f + (mc - k) for lag slot k of the chunk, two lags per
 // reciprocal, stored by store_group (groups cc0 .. cc0 + NG - 1 of the row).
@@ -377,9 +467,7 @@ __device__ __forceinline__ void gen_groups(uint32_t dst0, uint32_t dst1, uint32_
         }
     }
     wait();
-#pragma unroll
-    for (int cc = 0; cc < NG; ++cc)
-        store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv[cc], lv[cc], g0, g1);
+    store_row<NG, kSplit, kDst>(dst0, dst1, sw, cc0, hv, lv, g0, g1);
 }
 
 // Steering weights of NG groups (4 bins each) for this thread's row of A: the
@@ -419,9 +507,7 @@ __device__ __forceinline__ void gen_steer(uint32_t dst0, uint32_t dst1, uint32_t
         }
     }
     wait();
-#pragma unroll
-    for (int cc = 0; cc < NG; ++cc)
-        store_group<kSplit, kDst>(dst0, dst1, sw, (uint32_t)cc + cc0, hv[cc], lv[cc], g0, g1);
+    store_row<NG, kSplit, kDst>(dst0, dst1, sw, cc0, hv, lv, g0, g1);
 }
 
 }  // namespace
