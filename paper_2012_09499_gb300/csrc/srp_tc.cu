@@ -63,7 +63,7 @@ using namespace tc;
 // With xi32 the FP32 samples xi_q(n) (not sign-folded) also go to
 // xi32[frame][off[q] + t], for the FP32 re-scoring of the maximiser.
 template <int kFmt, bool kFromY>  // kFmt 0: bf16, 1: bf16 hi/lo split, 2: fp16
-__global__ void __launch_bounds__(128) k_gcc_samples_tc(
+__global__ void __launch_bounds__(128, 12) k_gcc_samples_tc(
     const float2 *__restrict__ src, int M, const int2 *__restrict__ pairs, int weighting, int Q,
     int K, const int32_t *__restrict__ nq, const int32_t *__restrict__ offc, int n_aux,
     const float2 *__restrict__ twid, uint16_t *__restrict__ xi16, int L_pad, int S_pad,
