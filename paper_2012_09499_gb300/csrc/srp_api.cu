@@ -205,6 +205,13 @@ srp_status make_layout(const srp_plan_desc *d, Layout &lay) {
     lay.b_xi32 = (lay.rescore && nyq) ? sizeof(float) * (size_t)lay.L_pad * lay.S_pad : 0;
     lay.b_rs = lay.rescore ? (sizeof(unsigned long long) * (1 + kRescoreCtas) + sizeof(int)) *
                                  (size_t)lay.L_pad : 0;
+    // the GCC samples of a Nyquist tensor-core plan with PHAT-weighted STFT
+    // input by the tensor-core IDFT where its shape allows (else the CUDA-core
+    // sample kernel)
+    lay.nmax_all = lay.max_nq + lay.n_aux;
+    lay.gcc_mma = lay.tc && nyq && d->weighting == SRP_WEIGHT_PHAT &&
+                  d->input_kind == SRP_IN_STFT && gcc_mma_fits(lay.K, lay.nmax_all);
+    lay.b_gtw = lay.gcc_mma ? gcc_mma_twiddle_bytes(lay.K, lay.nmax_all) : 0;
     lay.b_offc = lay.tc ? sizeof(int32_t) * lay.Q : 0;
     lay.b_xs = lay.tc ? sizeof(int2) * (size_t)lay.Q * (size_t)lay.J_pad : 0;
     lay.b_ctab = lay.tc ? sizeof(int4) * (size_t)lay.n_chunks : 0;
@@ -267,6 +274,7 @@ void release(srp_plan_s *h) {
     cudaFree(h->d_off);
     cudaFree(h->d_x);
     cudaFree(h->d_twid);
+    cudaFree(h->d_gtw);
     cudaFree(h->d_psi);
     cudaFree(h->d_xi);
     cudaFree(h->d_xi16);
@@ -455,6 +463,15 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
                                         best, psi32, s), "conventional operand kernel");
         h->stage_ran[kStageGcc] = 1;
         ++launches;
+    } else if (h->mode == SRP_MODE_NYQUIST && lay.gcc_mma) {
+        SRP_CUDA(launch_gcc_samples_mma(h->gtw_map, psi, from_y, lay.M, h->weighting, L,
+                                        lay.Q, lay.K, h->d_nq, h->d_offc,
+                                        lay.n_aux, lay.nmax_all, h->d_xi16, lay.L_pad, lay.Sc,
+                                        fmt, best, h->d_xi32, h->d_off, lay.S_pad, h->d_status,
+                                        s),
+                 "GCC sample kernel");
+        h->stage_ran[kStageGcc] = 1;
+        ++launches;
     } else if (h->mode == SRP_MODE_NYQUIST && lay.tc) {
         SRP_CUDA(launch_gcc_samples_tc(psi, from_y, lay.M, h->d_pairs, h->weighting, L, lay.Q,
                                        lay.K, h->d_nq, h->d_offc, lay.n_aux, h->d_twid,
@@ -611,6 +628,7 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
     SRP_ALLOC(h->d_off, L.b_off);
     SRP_ALLOC(h->d_x, L.b_x);
     SRP_ALLOC(h->d_twid, L.b_twid);
+    SRP_ALLOC(h->d_gtw, L.b_gtw);
     SRP_ALLOC(h->d_psi, L.b_psi);
     SRP_ALLOC(h->d_xi, L.b_xi);
     SRP_ALLOC(h->d_xi16, L.b_xi16);
@@ -665,6 +683,8 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
         if ((e = up(h->d_twid, tw.data(), L.b_twid)) != cudaSuccess)
             return bail(cuda_fail(e, "upload twiddles"));
     }
+    if (L.b_gtw && (e = gcc_mma_twiddles(L.K, L.nmax_all, h->d_gtw, h->gtw_map)) != cudaSuccess)
+        return bail(cuda_fail(e, "tensor-core IDFT twiddles"));
     // Padding rows and frames of the GCC-sample buffers stay zero for ever.
     if (L.b_xi && (e = cudaMemset(h->d_xi, 0, L.b_xi)) != cudaSuccess)
         return bail(cuda_fail(e, "clear GCC buffer"));

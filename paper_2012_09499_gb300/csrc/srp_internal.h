@@ -57,16 +57,18 @@ struct Layout {
     std::vector<char> streamed;  // per pair: its weights are resident and streamed
     bool tc = false;    // the Nyquist map runs on the tensor cores
     bool rescore = false;  // reduced-precision tensor-core plan choosing its maximiser in FP32
+    bool gcc_mma = false;  // Nyquist tensor-core plan: GCC samples by the tensor-core IDFT
+    int nmax_all = 0;      // largest N_q + N_aux (the IDFT's lag columns)
     std::vector<int32_t> offc;
     // byte counts of every device buffer, in allocation order
     size_t b_status = 0, b_offc = 0, b_xs = 0, b_ctab = 0, b_w = 0, b_woff = 0;
     size_t b_pairs = 0, b_nq = 0, b_off = 0, b_x = 0, b_twid = 0, b_psi = 0, b_xi = 0,
            b_xi16 = 0, b_xi32 = 0, b_rs = 0, b_part = 0, b_in_stage = 0, b_maps_stage = 0,
-           b_small_stage = 0;
+           b_small_stage = 0, b_gtw = 0;
     size_t total() const {
         return b_status + b_offc + b_xs + b_ctab + b_w + b_woff + b_pairs + b_nq + b_off + b_x +
                b_twid + b_psi + b_xi + b_xi16 + b_xi32 + b_rs + b_part + b_in_stage +
-               b_maps_stage + b_small_stage;
+               b_maps_stage + b_small_stage + b_gtw;
     }
 };
 
@@ -89,6 +91,8 @@ struct srp_plan_s {
     int32_t *d_off = nullptr;      // [Q] first GCC-sample row of pair q
     int32_t *d_x = nullptr;        // [Q][J_pad] TDOA in samples, fixed point with xf fraction bits
     float2 *d_twid = nullptr;      // [K] (cos, sin)(2 pi j / K)
+    uint16_t *d_gtw = nullptr;     // [2][N][K] the tensor-core IDFT's twiddle operand (hi, lo)
+    alignas(64) unsigned char gtw_map[128] = {};  // CUtensorMap of d_gtw
     // scratch (owned)
     float2 *d_psi = nullptr;       // [L_max][Q][Kb] cross spectra (STFT input only)
     float *d_xi = nullptr;         // [S_pad][L_pad] GCC samples, frames contiguous
@@ -183,6 +187,21 @@ cudaError_t launch_gcc_samples_tc(const float2 *src, bool from_y, int M, const i
                                   uint16_t *xi16, int L_pad, int S_pad, int fmt,
                                   unsigned long long *best, float *xi32, const int32_t *off,
                                   int S32, cudaStream_t s);
+// The same samples by the tensor-core inverse DFT (srp_gcc_mma.cu), for
+// PHAT-weighted STFT input (pairs in the plan's enumeration: m' outer, m > m'
+// inner), K a multiple of 64 and 2 nmax + 1 <= 256 lag columns (nmax: the
+// largest N_q + N_aux): gcc_mma_fits tells whether the shape qualifies, and
+// gcc_mma_twiddles writes its twiddle operand (gcc_mma_twiddle_bytes) and
+// the operand's tensor map at plan time.
+bool gcc_mma_fits(int K, int nmax);
+size_t gcc_mma_twiddle_bytes(int K, int nmax);
+cudaError_t gcc_mma_twiddles(int K, int nmax, uint16_t *d_tw, void *map_out);
+cudaError_t launch_gcc_samples_mma(const void *tw_map, const float2 *src, bool from_y, int M,
+                                   int weighting, int L, int Q, int K,
+                                   const int32_t *nq, const int32_t *offc, int n_aux, int nmax,
+                                   uint16_t *xi16, int L_pad, int S_pad, int fmt,
+                                   unsigned long long *best, float *xi32, const int32_t *off,
+                                   int S32, int *status, cudaStream_t s);
 int interp_tc_frames_per_cta(int L);
 // frame_keys (nullable, for the FP32 re-scoring): every tile writes its key
 // per frame to part[l][tile] and raises frame_keys[l] (cleared by the operand

@@ -120,6 +120,10 @@ def test_footprint_counts_every_buffer():
     x_tab = 4 * Q * Jp  # int32 TDOA table of the CUDA-core kernels
     # tensor-core engine: twiddles, 8-aligned pair offsets, split 16-bit GCC samples
     tc_tables = 4 * Q + 8 * Q * Jp + 16 * (Sc // 64)  # pair offsets, (TDOA, sp), chunk table
+    # the tensor-core IDFT's twiddle operand: (hi, lo) x N lag columns x K slots,
+    # N = 2 (max N_q + N_aux) + 1 rounded up to 32
+    Ng = -(-(2 * (int(nq.max()) + 2) + 1) // 32) * 32
+    tc_tables += 2 * 2 * Ng * 1024
     assert fp == common + 8 * 1024 + tc_tables + 2 * 2 * Lp * Sc
     d3, keep3 = _desc(M=8, J=1000, K=1024, max_frames=64, n_aux=2, engine="cuda_cores")
     Sp = -(-info.S // 64) * 64
