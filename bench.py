@@ -38,7 +38,7 @@ WORKLOAD = dict(name="room_3d", M=8, J=480000, K=1024, L=64, n_aux=2, fs=16000.0
 FLUSH_BYTES = 256 << 20
 # The sources of the single-plan tensor-core kernels, whose DRAM traffic a
 # recorded ncu capture describes.
-KERNEL_SOURCES = ("srp_tc.cu", "srp_tc_common.cuh", "srp_device.cuh")
+KERNEL_SOURCES = ("srp_tc.cu", "srp_tc_common.cuh", "srp_device.cuh", "srp_gcc_mma.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
 
@@ -375,9 +375,13 @@ def bench_ours(args):
     bf16_peak, peak_src = measured_bf16_peak()
     hbm_peak, hbm_src = measured_hbm_peak()
     # the GCC-sample stage (with the PHAT cross spectra): STFT frames in,
-    # 16-bit operand B out (hi and lo parts for the FP32 split)
+    # 16-bit operand B out (hi and lo parts for the FP32 split), and on the
+    # tensor cores the plan's twiddle operand (fp16 hi and lo, N lag rows x K)
     k2_ms = float(res["nyquist"]["stages"]["gcc_samples"])
-    k2_bytes = 8.0 * L * w["M"] * (w["K"] // 2 + 1) + 2.0 * 2.0 * L * S
+    k2_tc = bool(ny.info.gcc_tensor_cores)
+    n_lag = -(-(2 * (ny.info.max_nq + w["n_aux"]) + 1) // 32) * 32
+    k2_tw = 2.0 * 2.0 * n_lag * w["K"] if k2_tc else 0.0
+    k2_bytes = 8.0 * L * w["M"] * (w["K"] // 2 + 1) + 2.0 * 2.0 * L * S + k2_tw
 
     # reduced-precision variants of the same step (Nyquist, tensor cores)
     variants = {}
@@ -458,12 +462,18 @@ def bench_ours(args):
                                  "tensor_pipe_frac counts them, frac counts the method's flops"),
         },
         "roofline_gcc_samples": {
-            "kernel": "k_gcc_samples_tc<split, from STFT> (PHAT cross spectra + critical GCC samples)",
+            "kernel": ("k_gcc_samples_mma<split> (PHAT cross spectra + partial IDFT as an "
+                       "FP16-split tcgen05 contraction)" if k2_tc else
+                       "k_gcc_samples_tc<split, from STFT> (PHAT cross spectra + critical GCC "
+                       "samples)"),
             "bound": "hbm", "achieved": k2_bytes / (k2_ms * 1e-3) / 1e9, "peak": hbm_peak,
             "unit": "GB/s", "frac": k2_bytes / (k2_ms * 1e-3) / 1e9 / hbm_peak,
-            "traffic": recorded_traffic("k_gcc_samples_tc_fp32_room_3d"),
-            "algorithmic": (f"8*L*M*Kb STFT in + 2*2*L*S operand B out = {k2_bytes:.4g} B per "
-                            f"launch; {k2_ms:.4f} ms per launch"),
+            "traffic": recorded_traffic("k_gcc_samples_mma_fp32_room_3d" if k2_tc
+                                        else "k_gcc_samples_tc_fp32_room_3d"),
+            "algorithmic": (f"8*L*M*Kb STFT in + 2*2*L*S operand B out"
+                            + (f" + 2*2*{n_lag}*K twiddle operand" if k2_tc else "")
+                            + f" = {k2_bytes:.4g} B per launch; {k2_ms:.4f} ms per launch "
+                            "(stage time by CUDA events, launch latency included)"),
             "peak_source": f"measured HBM copy {hbm_peak:.0f} GB/s ({hbm_src})",
         },
         "precision_variants": variants,

@@ -160,6 +160,10 @@ typedef struct {
     int32_t accum_promotion; /* FP32 conventional maps on the tensor cores: every this many
                                 64-slot chunks of the reduction, the accumulators are added
                                 into FP32 sums and restarted (0: never) */
+    int32_t gcc_tensor_cores; /* 1: the critical GCC samples (Eq. GCC_IFT at tau = nT) are
+                                 the tensor cores' partial inverse DFT (Nyquist tensor-core
+                                 plans with PHAT-weighted STFT input, K a multiple of 64,
+                                 2 (max N_q + N_aux) + 1 <= 128); 0: CUDA cores */
 } srp_plan_info;
 
 typedef struct srp_plan_s *srp_handle;

@@ -259,6 +259,7 @@ void fill_info(const Layout &lay, srp_plan_info *info) {
     info->weight_bytes = lay.b_w;
     info->argmax_rescored = lay.rescore ? 1 : 0;
     info->accum_promotion = lay.promote;
+    info->gcc_tensor_cores = lay.gcc_mma ? 1 : 0;
 }
 
 template <typename T>
@@ -468,7 +469,7 @@ srp_status run_map(srp_plan_s *h, const void *d_in, int L, float *d_maps, int32_
                                         lay.Q, lay.K, h->d_nq, h->d_offc,
                                         lay.n_aux, lay.nmax_all, h->d_xi16, lay.L_pad, lay.Sc,
                                         fmt, best, h->d_xi32, h->d_off, lay.S_pad, h->d_status,
-                                        s),
+                                        h->gcc_zmax, s),
                  "GCC sample kernel");
         h->stage_ran[kStageGcc] = 1;
         ++launches;
@@ -683,8 +684,13 @@ srp_status srp_plan(const srp_plan_desc *d, srp_handle *out) {
         if ((e = up(h->d_twid, tw.data(), L.b_twid)) != cudaSuccess)
             return bail(cuda_fail(e, "upload twiddles"));
     }
-    if (L.b_gtw && (e = gcc_mma_twiddles(L.K, L.nmax_all, h->d_gtw, h->gtw_map)) != cudaSuccess)
-        return bail(cuda_fail(e, "tensor-core IDFT twiddles"));
+    if (L.b_gtw) {
+        if ((e = gcc_mma_twiddles(L.K, L.nmax_all, h->d_gtw, h->gtw_map)) != cudaSuccess)
+            return bail(cuda_fail(e, "tensor-core IDFT twiddles"));
+        const int fmt = h->precision == SRP_PREC_FP32 ? 1 : (h->precision == SRP_PREC_FP16 ? 2 : 0);
+        if ((h->gcc_zmax = gcc_mma_setup(L.K, L.nmax_all, fmt)) == 0)
+            return bail(cuda_fail(cudaErrorInvalidValue, "tensor-core IDFT set-up"));
+    }
     // Padding rows and frames of the GCC-sample buffers stay zero for ever.
     if (L.b_xi && (e = cudaMemset(h->d_xi, 0, L.b_xi)) != cudaSuccess)
         return bail(cuda_fail(e, "clear GCC buffer"));

@@ -50,9 +50,16 @@ using namespace dev;
 using namespace tc;
 
 constexpr int kGmThreads = 512;   // 16 warps: A formation, then the epilogue
-constexpr int kGmHead = 4096;     // barriers and the reduced rows' tables
-constexpr int kGmMaxZ = 8;        // CTAs per cluster (a portable cluster size)
+constexpr int kGmHead = 8192;     // barriers, the rows' spectrum pointers and tables
+constexpr int kGmMaxZ = 16;       // CTAs per cluster: 16 where the GPU schedules it, else 8
+constexpr int kGmPortableZ = 8;
 constexpr int kGmSmemMax = 227 * 1024;
+// TMEM columns per CTA.  A CTA waits at the cluster barriers for the other
+// CTAs of its cluster, which may share its SM; with at most 2048 / 512 = 4
+// CTAs of this kernel per SM and 128 columns each, every CTA's allocation
+// succeeds whichever of them share an SM, so no CTA can wait for columns
+// that a CTA waiting on it holds.
+constexpr uint32_t kGmTmemCols = 128;
 
 struct GmArgs {
     const float2 *src;      // STFT frames [L][M][Kb] (kFromY) or cross spectra [L][Q][Kb]
@@ -70,7 +77,6 @@ struct GmArgs {
     int n_acc;              // TMEM accumulators (N columns each) the 16-slot steps rotate over
     int L_pad, S_pad, S32;
     uint32_t idesc;
-    uint32_t tmem_cols;
     uint32_t a_bytes;       // A region (cpz x (hi, lo) tiles, or the partial sums if larger)
 };
 
@@ -103,15 +109,16 @@ __device__ __forceinline__ float2 cross_bin(const GmArgs &a, int l, int q, int k
 }
 
 template <int kFmt, bool kFromY>
-__global__ void __launch_bounds__(kGmThreads, 1)
+__global__ void __launch_bounds__(kGmThreads, 2)
     k_gcc_samples_mma(const __grid_constant__ CUtensorMap tmap, const GmArgs a) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *gbase = smem_raw + (base - raw);
-    // [0, 1024): barriers, TMEM address, abort flag; [1024, 4096): the tables
-    // of the rows this CTA reduces; then the A region (A_hi, A_lo of each
-    // chunk, 16 KB each; later the partial sums), then B
+    // [0, 1024): barriers, TMEM address, abort flag; [1024, 3072): the tables
+    // of the rows this CTA reduces; [4096, 8192): the spectrum pointers of
+    // the tile's rows; then the A region (A_hi, A_lo of each chunk, 16 KB
+    // each; later the partial sums), then B
     const uint32_t full_bar = base, mma_bar = base + 8;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gbase + 16);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + 20);
@@ -119,6 +126,8 @@ __global__ void __launch_bounds__(kGmThreads, 1)
     int *row_nmq = reinterpret_cast<int *>(gbase + 1536);           // [128] N_q + N_aux (-1: none)
     int *row_o16 = reinterpret_cast<int *>(gbase + 2048);           // [128] l S_pad + offc[q]
     int *row_o32 = reinterpret_cast<int *>(gbase + 2560);           // [128] l S32 + off[q]
+    // [128] the row's two spectra (STFT rows of mics m, m'; null past the last row)
+    const float2 **row_sp = reinterpret_cast<const float2 **>(gbase + 4096);
     const uint32_t a0 = base + (uint32_t)kGmHead;
     const uint32_t b0 = a0 + a.a_bytes;
     const uint32_t b_tile = (uint32_t)a.N * 128u;
@@ -137,7 +146,23 @@ __global__ void __launch_bounds__(kGmThreads, 1)
         *abort_flag = 0;
         fence_barrier_init();
     }
-    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kGmTmemCols);
+    if (threadIdx.x >= kGmThreads - 128) {  // the last four warps: one tile row each
+        const int r = (int)threadIdx.x - (kGmThreads - 128), rg = tile * 128 + r;
+        const float2 *p0 = nullptr, *p1 = nullptr;
+        if (rg < R) {
+            const int l = rg / a.Q, q = rg - l * a.Q;
+            if (kFromY) {
+                const int2 p = pair_of(q, a.M);
+                p0 = a.src + ((size_t)l * a.M + p.x) * Kb;
+                p1 = a.src + ((size_t)l * a.M + p.y) * Kb;
+            } else {
+                p0 = a.src + ((size_t)l * a.Q + q) * Kb;
+            }
+        }
+        row_sp[2 * r] = p0;
+        row_sp[2 * r + 1] = p1;
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -158,65 +183,46 @@ __global__ void __launch_bounds__(kGmThreads, 1)
     // ---- A: warp w forms rows w, w + 16, ..., lane = bin of the chunk ----
     // (re, im) of bin 32 chunk + lane are slots 2 lane, 2 lane + 1 of the chunk:
     // bytes 4 lane of the row's 128, in 16-byte unit (lane >> 2) ^ (row & 7).
-    // Every load of a pass (kGmRows rows x up to two chunks) is issued before
-    // any arithmetic, so that one memory latency covers the pass.
+    // Every load of a chunk (the warp's 8 rows, both spectra) is issued before
+    // any arithmetic, so that one memory latency covers the chunk.
     constexpr int kRowsW = 128 / (kGmThreads / 32);  // rows per warp
-    const float2 *rp0[kRowsW], *rp1[kRowsW];         // the row's two spectra (one without kFromY)
+    for (int cc = 0; cc < a.cpz; ++cc) {
+        const int k = (chunk0 + cc) * 32 + lane;
+        float2 x[kRowsW], y[kRowsW];
 #pragma unroll
-    for (int j = 0; j < kRowsW; ++j) {
-        const int rg = tile * 128 + warp + (kGmThreads / 32) * j;
-        rp0[j] = rp1[j] = nullptr;
-        if (rg < R) {
-            const int l = rg / a.Q, q = rg - l * a.Q;
-            if (kFromY) {
-                const int2 p = pair_of(q, a.M);
-                rp0[j] = a.src + ((size_t)l * a.M + p.x) * Kb;
-                rp1[j] = a.src + ((size_t)l * a.M + p.y) * Kb;
-            } else {
-                rp0[j] = a.src + ((size_t)l * a.Q + q) * Kb;
+        for (int j = 0; j < kRowsW; ++j) {
+            const int r = warp + (kGmThreads / 32) * j;
+            const float2 *p0 = row_sp[2 * r], *p1 = row_sp[2 * r + 1];
+            x[j] = y[j] = make_float2(0.0f, 0.0f);
+            if (p0 != nullptr) {
+                x[j] = __ldg(p0 + k);
+                if (kFromY) y[j] = __ldg(p1 + k);
             }
         }
-    }
-    for (int cc0 = 0; cc0 < a.cpz; cc0 += 2) {
-        float2 x[kRowsW][2], y[kRowsW][2];
 #pragma unroll
-        for (int j = 0; j < kRowsW; ++j)
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int k = (chunk0 + cc0 + u) * 32 + lane;
-                x[j][u] = y[j][u] = make_float2(0.0f, 0.0f);
-                if (rp0[j] != nullptr && cc0 + u < a.cpz) {
-                    x[j][u] = __ldg(rp0[j] + k);
-                    if (kFromY) y[j][u] = __ldg(rp1[j] + k);
+        for (int j = 0; j < kRowsW; ++j) {
+            float2 v = x[j];
+            if (kFromY) {
+                float2 w = y[j];
+                if (a.weighting == SRP_WEIGHT_PHAT) {
+                    v = unit_phase(v);
+                    w = unit_phase(w);
                 }
+                v = times_conj(v, w);
             }
-#pragma unroll
-        for (int j = 0; j < kRowsW; ++j)
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                if (cc0 + u >= a.cpz) continue;
-                float2 v = x[j][u];
-                if (kFromY) {
-                    float2 w = y[j][u];
-                    if (a.weighting == SRP_WEIGHT_PHAT) {
-                        v = unit_phase(v);
-                        w = unit_phase(w);
-                    }
-                    v = times_conj(v, w);
-                }
-                const int r = warp + (kGmThreads / 32) * j;
-                const __half2 h2 = __floats2half2_rn(v.x, v.y);
-                const float2 hf = __half22float2(h2);
-                const uint32_t hi = *reinterpret_cast<const uint32_t *>(&h2);
-                const float2 lo = make_float2(v.x - hf.x, v.y - hf.y);
-                const uint32_t addr = a0 + (uint32_t)(cc0 + u) * 2u * kATile + (uint32_t)r * 128u +
-                                      ((((uint32_t)lane >> 2) ^ ((uint32_t)r & 7u)) << 4) +
-                                      ((uint32_t)lane & 3u) * 4u;
-                asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(hi) : "memory");
-                asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr + kATile),
-                             "r"(pack_f16(lo.x, lo.y))
-                             : "memory");
-            }
+            const int r = warp + (kGmThreads / 32) * j;
+            const __half2 h2 = __floats2half2_rn(v.x, v.y);
+            const float2 hf = __half22float2(h2);
+            const uint32_t hi = *reinterpret_cast<const uint32_t *>(&h2);
+            const float2 lo = make_float2(v.x - hf.x, v.y - hf.y);
+            const uint32_t addr = a0 + (uint32_t)cc * 2u * kATile + (uint32_t)r * 128u +
+                                  ((((uint32_t)lane >> 2) ^ ((uint32_t)r & 7u)) << 4) +
+                                  ((uint32_t)lane & 3u) * 4u;
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(hi) : "memory");
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr + kATile),
+                         "r"(pack_f16(lo.x, lo.y))
+                         : "memory");
+        }
     }
     fence_proxy_async();  // A's generic stores before the tensor core reads them
     __syncthreads();
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
         }
     }
     cluster.sync();  // no CTA leaves while another still reads its partial sums
-    if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+    if (warp == 0) tmem_dealloc(tmem, kGmTmemCols);
 }
 
 // IEEE half precision of x (|x| < 65504), rounded to nearest even, and back.
@@ -365,13 +371,15 @@ struct GmShape {
     size_t smem = 0;
 };
 
-GmShape gm_shape(int K, int nmax) {
+// zmax: the largest cluster the launch may use (8, or 16 where supported);
+// plan-time checks use 8, whose CTAs need the most shared memory.
+GmShape gm_shape(int K, int nmax, int zmax = kGmPortableZ) {
     GmShape g;
     if (K % kChunk != 0 || K < kChunk) return g;
     const int n_chunks = K / kChunk;  // 32 bins (64 slots) per chunk; the Nyquist bin apart
     const int N = (2 * nmax + 1 + 31) / 32 * 32;
-    if (N > 256) return g;
-    int Z = std::min(kGmMaxZ, n_chunks);
+    if (N > (int)kGmTmemCols) return g;
+    int Z = std::min(zmax, n_chunks);
     while (n_chunks % Z != 0) --Z;
     const int cpz = n_chunks / Z;
     const size_t a_tiles = (size_t)cpz * 2 * kATile;
@@ -387,7 +395,47 @@ GmShape gm_shape(int K, int nmax) {
     return g;
 }
 
+typedef void (*GmKern)(const CUtensorMap, const GmArgs);
+
+GmKern gm_kernel(int fmt) {
+    static const GmKern kerns[3] = {k_gcc_samples_mma<0, true>, k_gcc_samples_mma<1, true>,
+                                    k_gcc_samples_mma<2, true>};
+    return kerns[fmt];
+}
+
 }  // namespace
+
+int gcc_mma_setup(int K, int nmax, int fmt) {
+    if (fmt < 0 || fmt > 2 || gm_shape(K, nmax).N == 0) return 0;
+    const GmKern k = gm_kernel(fmt);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kGmSmemMax) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    // a cluster of 16 where the GPU can place one of this shape, else the portable 8
+    int zmax = kGmPortableZ;
+    const GmShape g = gm_shape(K, nmax, kGmMaxZ);
+    if (g.Z == kGmMaxZ &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t q = {};
+        q.gridDim = dim3((unsigned)g.Z, 1);
+        q.blockDim = dim3(kGmThreads);
+        q.dynamicSmemBytes = g.smem;
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = (unsigned)g.Z;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        int n_clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&n_clusters, k, &q) == cudaSuccess && n_clusters > 0)
+            zmax = kGmMaxZ;
+    }
+    (void)cudaGetLastError();
+    return zmax;
+}
 
 bool gcc_mma_fits(int K, int nmax) { return gm_shape(K, nmax).N > 0; }
 
@@ -427,9 +475,11 @@ cudaError_t launch_gcc_samples_mma(const void *tw_map, const float2 *src, bool f
                                    const int32_t *nq, const int32_t *offc, int n_aux, int nmax,
                                    uint16_t *xi16, int L_pad, int S_pad, int fmt,
                                    unsigned long long *best, float *xi32, const int32_t *off,
-                                   int S32, int *status, cudaStream_t s) {
+                                   int S32, int *status, int zmax, cudaStream_t s) {
     if (L == 0) return cudaSuccess;
-    const GmShape g = gm_shape(K, nmax);
+    if (!from_y || weighting != SRP_WEIGHT_PHAT || fmt < 0 || fmt > 2) return cudaErrorInvalidValue;
+    const int v = fmt;
+    const GmShape g = gm_shape(K, nmax, zmax);
     if (g.N == 0) return cudaErrorInvalidValue;
     GmArgs a;
     a.src = src;
@@ -455,23 +505,8 @@ cudaError_t launch_gcc_samples_mma(const void *tw_map, const float2 *src, bool f
     // kind::f16: FP32 accumulate (bit 4), A and B FP16 (0 at bits 7, 10), both
     // K-major, N >> 3 at bit 17, M = 128 >> 4 at bit 24
     a.idesc = (1u << 4) | ((uint32_t)(g.N >> 3) << 17) | ((128u >> 4) << 24);
-    a.n_acc = std::max(1, std::min(g.cpz * (kChunk / 16), 512 / g.N));
-    uint32_t cols = 32;
-    while (cols < (uint32_t)(a.n_acc * g.N)) cols <<= 1;
-    a.tmem_cols = cols;
+    a.n_acc = std::max(1, std::min(g.cpz * (kChunk / 16), (int)kGmTmemCols / g.N));
     a.a_bytes = g.a_bytes;
-    typedef void (*Kern)(const CUtensorMap, const GmArgs);
-    if (!from_y || weighting != SRP_WEIGHT_PHAT) return cudaErrorInvalidValue;
-    static const Kern kerns[3] = {k_gcc_samples_mma<0, true>, k_gcc_samples_mma<1, true>,
-                                  k_gcc_samples_mma<2, true>};
-    static bool attr[3] = {false, false, false};
-    const int v = fmt;
-    if (!attr[v]) {
-        cudaError_t e = cudaFuncSetAttribute(kerns[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kGmSmemMax);
-        if (e != cudaSuccess) return e;
-        attr[v] = true;
-    }
     const int tiles = (L * Q + 127) / 128;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)g.Z, (unsigned)tiles);
@@ -486,7 +521,7 @@ cudaError_t launch_gcc_samples_mma(const void *tw_map, const float2 *src, bool f
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(tw_map);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kerns[v], map, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, gm_kernel(v), map, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -93,6 +93,7 @@ struct srp_plan_s {
     float2 *d_twid = nullptr;      // [K] (cos, sin)(2 pi j / K)
     uint16_t *d_gtw = nullptr;     // [2][N][K] the tensor-core IDFT's twiddle operand (hi, lo)
     alignas(64) unsigned char gtw_map[128] = {};  // CUtensorMap of d_gtw
+    int gcc_zmax = 0;              // cluster size limit of the tensor-core IDFT
     // scratch (owned)
     float2 *d_psi = nullptr;       // [L_max][Q][Kb] cross spectra (STFT input only)
     float *d_xi = nullptr;         // [S_pad][L_pad] GCC samples, frames contiguous
@@ -189,11 +190,15 @@ cudaError_t launch_gcc_samples_tc(const float2 *src, bool from_y, int M, const i
                                   int S32, cudaStream_t s);
 // The same samples by the tensor-core inverse DFT (srp_gcc_mma.cu), for
 // PHAT-weighted STFT input (pairs in the plan's enumeration: m' outer, m > m'
-// inner), K a multiple of 64 and 2 nmax + 1 <= 256 lag columns (nmax: the
+// inner), K a multiple of 64 and 2 nmax + 1 <= 128 lag columns (nmax: the
 // largest N_q + N_aux): gcc_mma_fits tells whether the shape qualifies, and
 // gcc_mma_twiddles writes its twiddle operand (gcc_mma_twiddle_bytes) and
 // the operand's tensor map at plan time.
 bool gcc_mma_fits(int K, int nmax);
+// Plan time: set the kernel's attributes for output format fmt (0 bf16, 1
+// bf16 split, 2 fp16) and return the cluster size limit the launches use
+// (16 where the GPU can place such a cluster, else 8; 0 on failure).
+int gcc_mma_setup(int K, int nmax, int fmt);
 size_t gcc_mma_twiddle_bytes(int K, int nmax);
 cudaError_t gcc_mma_twiddles(int K, int nmax, uint16_t *d_tw, void *map_out);
 cudaError_t launch_gcc_samples_mma(const void *tw_map, const float2 *src, bool from_y, int M,
@@ -201,7 +206,7 @@ cudaError_t launch_gcc_samples_mma(const void *tw_map, const float2 *src, bool f
                                    const int32_t *nq, const int32_t *offc, int n_aux, int nmax,
                                    uint16_t *xi16, int L_pad, int S_pad, int fmt,
                                    unsigned long long *best, float *xi32, const int32_t *off,
-                                   int S32, int *status, cudaStream_t s);
+                                   int S32, int *status, int zmax, cudaStream_t s);
 int interp_tc_frames_per_cta(int L);
 // frame_keys (nullable, for the FP32 re-scoring): every tile writes its key
 // per frame to part[l][tile] and raises frame_keys[l] (cleared by the operand

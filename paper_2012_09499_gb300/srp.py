@@ -52,6 +52,7 @@ class srp_plan_info(ctypes.Structure):
         ("max_frames", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
         ("device_bytes", ctypes.c_size_t), ("weight_bytes", ctypes.c_size_t),
         ("argmax_rescored", ctypes.c_int32), ("accum_promotion", ctypes.c_int32),
+        ("gcc_tensor_cores", ctypes.c_int32),
     ]
 
 

@@ -310,3 +310,33 @@ def test_static_gcc_samples_checks_before_any_cuda_call():
         args = (M, K, n_aux, nq.ctypes.data if M == 4 else np.zeros(136, np.int32).ctypes.data,
                 None, frames, None, None)
         assert L.srp_gcc_samples_static(*args) == srp.SRP_ERR_INVALID_ARG, (M, K, frames)
+
+
+def test_gcc_engine_choice():
+    """The critical GCC samples run as the tensor cores' partial inverse DFT
+    for Nyquist tensor-core plans with PHAT-weighted STFT input, K a multiple
+    of 64 and at most 128 lag columns (2 (max N_q + N_aux) + 1); every other
+    plan forms them on the CUDA cores."""
+    rng = np.random.default_rng(7)
+    mic = rng.uniform(-0.25, 0.25, (8, 3))
+    grid = rng.uniform(0, 5, (100, 3))
+
+    def engine(mic_=mic, K=1024, **kw):
+        d, keep = srp.make_desc(mic_, grid, 16000.0, 343.0, K, **kw)
+        return srp.srp_plan_describe(d)[0].gcc_tensor_cores
+
+    assert engine() == 1
+    assert engine(precision="bf16") == 1 and engine(precision="fp16") == 1
+    assert engine(K=2048) == 1 and engine(K=64 * 15) == 1
+    assert engine(weighting="none") == 0
+    assert engine(input_kind="cross") == 0
+    assert engine(mode="conventional") == 0
+    assert engine(engine="cuda_cores") == 0
+    assert engine(K=1000) == 0  # not a multiple of 64
+    # lag columns 2 (max N_q + N_aux) + 1 against the limit of 128: apertures
+    # of 0.9 m (87 columns), 1.5 m (143) and 5 m at 16 kHz
+    for width, tc in ((0.9, 1), (1.5, 0), (5.0, 0)):
+        wide = np.array([[0.0, 0.0, 0.0], [width, 0.0, 0.0], [0.0, 0.3, 0.0]])
+        info, nq = srp.srp_plan_describe(srp.make_desc(wide, grid, 16000.0, 343.0, 1024)[0])
+        assert (2 * (int(nq.max()) + 2) + 1 <= 128) == bool(tc)
+        assert info.gcc_tensor_cores == tc, width
