@@ -502,6 +502,12 @@ def bench_ours(args):
                 "tensor_core_streams": v["tensor_core_streams"],
                 "overlapped_iterations_frac": v["overlapped_iterations_frac"]}
             for k, v in extra["serving"].items() if isinstance(v, dict) and "p99_ms" in v}
+    if "batched" in extra:  # and of the batched uneven mix
+        line["batched_summary"] = {
+            k: {"value": v["value"], "unit": v["unit"], "ms_per_step": v["ms_per_step"],
+                "stage_ms": v["stage_ms"], "roofline_frac": v["roofline"]["frac"],
+                "roofline_unit": v["roofline"]["unit"]}
+            for k, v in extra["batched"].items() if isinstance(v, dict) and "roofline" in v}
     print(json.dumps(line))
 
 
